@@ -1,0 +1,399 @@
+#!/usr/bin/env python
+"""Benchmark of the smearing + meson chain on GB300 (one JSON line on stdout).
+
+One step is one pass of the whole path on the 16^3x32 workload (the shape of
+the paper's run A, Fig. 4a), single precision storage:
+
+  1. field setup: import the synthetic propagator (stand-in for the solver
+     output, which is out of scope) from its canonical layout, and create the
+     point source;
+  2. SRC: Gaussian smearing of the point source, kappa = 0.21, N = 25;
+  3. SNK: Gaussian smearing of the propagator, kappa = 0.21, N = 25;
+  4. HAD: the sixteen meson correlators at zero momentum with FP64
+     timeslice sums.
+
+``value`` is the algorithmic bytes of a step (each field read and written
+once per pass, links read once per smearing iteration) divided by the
+device time per step, with inputs resident in HBM.  ``e2e`` is the same
+quantity through the public API with the inputs copied from pinned host
+memory and the correlators read back every step.
+
+``--impl reference`` times the FP64 checker on the host cores on a bounded
+sample of the same workload (one timeslice per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "smear GB/s (%HBM peak), contraction sites/s; BF16 vs FP32 batched at tol"
+CSRC = os.path.join(ROOT, "paper_1111_5596_gb300", "csrc")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0,
+                    help="minimum host time of the checker baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workload bookkeeping (shared by both arms)
+
+
+def workload():
+    from synth import configs
+
+    return configs.MESONS_16x32
+
+
+def step_bytes(w, n_timeslices=None) -> dict:
+    """Algorithmic bytes per step (FP32 storage) for all or some timeslices."""
+    V = w.V3 * (w.Nt if n_timeslices is None else n_timeslices)
+    prop = V * 144 * 8
+    hop = V * (144 * 8 * 2 + 3 * 9 * 8)          # read psi, write psi, 3 spatial links
+    b = {
+        "import": 2 * prop,                      # canonical read + device-layout write
+        "point_source": prop,                    # write
+        "smear_src": w.n_smear * hop,
+        "smear_snk": w.n_smear * hop,
+        "mesons": prop,                          # S1 = S2: one read
+    }
+    b["total"] = sum(b.values())
+    b["hop_per_launch"] = hop
+    return b
+
+
+# ---------------------------------------------------------------------------
+# host FP64 checker arm
+
+
+def run_checker_sample(w, t: int, U64, P64):
+    """The FP64 checker on one timeslice of the step: SRC, SNK, 16 mesons."""
+    from oracle import hadron, smear, source
+
+    sub = (w.dims[0], w.dims[1], w.dims[2], 1)
+    Ut = U64[:, t:t + 1]
+    src = smear.gauss_smear(Ut, source.point_propagator(sub), w.kappa, w.n_smear, 3)
+    snk = smear.gauss_smear(Ut, P64[t:t + 1], w.kappa, w.n_smear, 3)
+    C = hadron.meson_2pt(snk, snk, hadron.SIXTEEN_MESONS)
+    return src, snk, C
+
+
+def checker_inputs(w, t0: int, t1: int):
+    from synth import fields
+
+    U = fields.round_to_f32(fields.gauge_field(w.dims, w.seed, kind=w.links, eps=w.eps, x3_range=(t0, t1)))
+    U = U.reshape((4, t1 - t0) + U.shape[2:])
+    P = fields.round_to_f32(fields.propagator(w.dims, w.seed, x3_range=(t0, t1)))
+    return U, P
+
+
+def cpu_baseline(w, min_seconds: float) -> dict:
+    """Time the checker on whole timeslices until min_seconds of host time."""
+    U, P = checker_inputs(w, 0, 4)
+    done, t_total = 0, 0.0
+    while done < 4 and (t_total < min_seconds or done == 0):
+        t0 = time.perf_counter()
+        run_checker_sample(w, done, U, P)
+        t_total += time.perf_counter() - t0
+        done += 1
+    b = step_bytes(w, n_timeslices=done)["total"]
+    return {"value": b / t_total / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": f"{done} of {w.Nt} timeslices of the step (SRC + SNK smearing N={w.n_smear}, "
+                      f"16 mesons), numpy FP64, {t_total:.1f} s"}
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload()
+    U, P = checker_inputs(w, 0, 1)
+    for _ in range(args.warmup):
+        run_checker_sample(w, 0, U, P)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        run_checker_sample(w, 0, U, P)
+    dt = (time.perf_counter() - t0) / args.steps
+    b = step_bytes(w, n_timeslices=1)["total"]
+    value = b / dt / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_block(w),
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": f"1 of {w.Nt} timeslices per step (SRC + SNK smearing N={w.n_smear}, "
+                                   f"16 mesons), numpy FP64"},
+        "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_block(w) -> dict:
+    L0, L1, L2, L3 = w.dims
+    return {"workload": w.name, "lattice": f"{L0}x{L1}x{L2}x{L3}", "kappa": w.kappa, "n_smear": w.n_smear,
+            "links": f"{w.links} SU(3) eps={w.eps}", "storage": "f32 propagator, f32 links",
+            "stages": "import + point source + SRC smear + SNK smear + 16 mesons p=0",
+            "l2": "inputs larger than L2 (151 MB propagator per field vs 129 MB L2)",
+            "parallelism": "independent replica per GPU"}
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index  # nvidia-smi --id: the GPU's UUID, else its index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for n, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": d["hbm_gbs"], "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def traffic_for(kernel: str):
+    """ncu DRAM bytes per launch, if captured on the current kernel source."""
+    if not os.path.exists(TRAFFIC_FILE):
+        return None
+    with open(TRAFFIC_FILE) as f:
+        d = json.load(f).get(kernel)
+    if not d:
+        return None
+    with open(os.path.join(CSRC, d["source"]), "rb") as f:
+        sha = hashlib.sha256(f.read()).hexdigest()
+    return d["bytes_per_launch"] if sha == d["source_sha256"] else None
+
+
+def gpu_arm(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1111_5596_gb300 as q
+    from synth import configs, fields
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    q.load()
+
+    base = workload()
+    w = configs.Workload(base.name, base.dims, base.links, base.kappa, base.n_smear, base.prop, eps=base.eps,
+                         seed=base.seed + 1000 * rank)          # independent problem per rank
+    lat = q.Lattice(w.dims, w.j_decay)
+    U_h = torch.from_numpy(fields.gauge_field(w.dims, w.seed, kind=w.links, eps=w.eps).astype(np.complex64))
+    P_h = torch.from_numpy(fields.propagator(w.dims, w.seed).astype(np.complex64))
+    U_h, P_h = U_h.pin_memory(), P_h.pin_memory()
+    U_dev, P_dev = U_h.to(dev), P_h.to(dev)
+
+    U = q.Field(lat, q.GAUGE, q.F32, device=dev).import_(U_dev)
+    src = q.Field(lat, q.PROPAGATOR, q.F32, device=dev)
+    snk = q.Field(lat, q.PROPAGATOR, q.F32, device=dev)
+    scratch = q.Field(lat, q.PROPAGATOR, q.F32, device=dev)
+    C = torch.empty((16, 1, w.Nt), dtype=torch.complex128, device=dev)
+    C_h = torch.empty_like(C, device="cpu").pin_memory()
+
+    def step_device():
+        snk.import_(P_dev)
+        q.point_source(src)
+        q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
+        q.gauss_smear(U, snk, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
+        q.meson_2pt(snk, snk, q.SIXTEEN_MESONS, out=C)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def max_over_ranks(x: float) -> float:
+        if world == 1:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step_device()
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    try:
+        gpu_id = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except AttributeError:
+        gpu_id = str(local)
+    clocks = ClockSampler(gpu_id)
+    clocks.start()
+    q.profile_reset()
+    q.profile_enable(True)
+    launches0 = q.launch_count()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step_device()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = q.launch_count() - launches0
+    q.profile_enable(False)
+    clk = clocks.stop()
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    kern = {name: q.profile_query(name) for name in ("smear_hop", "meson_2pt", "field_import", "point_source")}
+
+    b = step_bytes(w)
+    peaks = measured_peaks()
+    value = world * b["total"] / (ms * 1e-3) / 1e9
+
+    hop_ms, hop_n = kern["smear_hop"]
+    hop_avg_s = hop_ms / hop_n * 1e-3
+    achieved = b["hop_per_launch"] / hop_avg_s / 1e9
+    mes_ms, mes_n = kern["meson_2pt"]
+    smear_s = hop_ms * 1e-3 / args.steps
+    roofline = {"kernel": "smear_hop (FP32 propagator, 12 columns)", "bound": "hbm", "achieved": achieved,
+                "peak": peaks["hbm_gbs"], "unit": "GB/s", "frac": achieved / peaks["hbm_gbs"],
+                "peak_source": peaks["source"], "traffic": traffic_for("smear_hop"),
+                "algorithmic_bytes_per_launch": b["hop_per_launch"], "avg_launch_us": hop_avg_s * 1e6,
+                "launches": hop_n}
+    components = {
+        "smear_gbs_kernel": (b["smear_src"] + b["smear_snk"]) / smear_s / 1e9,
+        "smear_hbm_frac": achieved / peaks["hbm_gbs"],
+        "contraction_sites_per_s": w.V / (mes_ms / mes_n * 1e-3),
+        "contraction_gbs": b["mesons"] / (mes_ms / mes_n * 1e-3) / 1e9,
+        "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
+    }
+
+    # ---- end to end through the public API, host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        U_stage = torch.empty_like(U_dev)
+        P_stage = torch.empty_like(P_dev)
+
+        def step_e2e():
+            U_stage.copy_(U_h, non_blocking=True)
+            P_stage.copy_(P_h, non_blocking=True)
+            U.import_(U_stage)
+            snk.import_(P_stage)
+            q.point_source(src)
+            q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
+            q.gauss_smear(U, snk, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
+            q.meson_2pt(snk, snk, q.SIXTEEN_MESONS, out=C)
+            C_h.copy_(C, non_blocking=True)
+            stream.synchronize()
+            return C_h
+
+        for _ in range(args.warmup):
+            step_e2e()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step_e2e()
+        barrier()
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        h2d = U_h.numel() * U_h.element_size() + P_h.numel() * P_h.element_size()
+        e2e = {"value": world * b["total"] / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": C_h.numel() * C_h.element_size(), "ms_per_step": e2e_s * 1e3}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(w, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded near-unit SU(3) links (eps=0.3) and Gaussian propagator with "
+                    "exp(-0.5|x|) envelope, complex64",
+            "config": config_block(w), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": clk, "components": components,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        reference_arm(args)
+    else:
+        gpu_arm(args)
+
+
+if __name__ == "__main__":
+    main()

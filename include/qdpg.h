@@ -1,0 +1,196 @@
+/*
+ * qdpg -- lattice-wide Gaussian smearing and hadron contractions on GB300.
+ *
+ * C ABI of libqdpg.so.  The operations are the data-parallel stages that
+ * Winter, "Accelerating QDP++/Chroma on GPUs" (Lattice 2011), moves from the
+ * host to the GPU: source creation, source/sink smearing and the hadron
+ * spectrum (Sec. 5, Fig. 4), expressed on QDP++-style lattice-wide fields
+ * (Sec. 1: data-parallel types over the whole lattice).
+ *
+ * General rules
+ * -------------
+ *  - Every call returns a qdpg_status (0 = OK).  On failure the thread-local
+ *    message is available from qdpg_last_error().  No C++ exception crosses
+ *    this interface.
+ *  - Device memory is owned by the caller (PyTorch in the Python binding).
+ *    The library never frees caller memory.  A qdpg_field_t only BORROWS the
+ *    device pointer it wraps.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls are asynchronous with respect to the host unless stated.
+ *  - Pointers documented as "device" must be device (or managed) memory of
+ *    the current CUDA device; passing host memory is undefined.
+ *
+ * Lattice and device layout
+ * -------------------------
+ *  A lattice has extents dims[0..3] (x0 fastest in the canonical site order)
+ *  and a decay direction j_decay (the "time" direction, 0..3).  On the
+ *  device every field is stored timeslice-major, component-major,
+ *  site-fastest ("SoA"):
+ *
+ *      element(t, comp, s3) at index (t * ncomp + comp) * V3 + s3
+ *
+ *  where t = x[j_decay], s3 is the lexicographic index of the other three
+ *  coordinates (increasing direction order, first one fastest) and V3 is
+ *  their product.  An element is one complex number: float2 (QDPG_F32) or a
+ *  pair of bfloat16 (QDPG_BF16, real part first).
+ *
+ *  Components per site (ncomp):
+ *    QDPG_COLOR_MATRIX  9    comp = a*3 + b                     (U[a][b])
+ *    QDPG_GAUGE        36    comp = mu*9 + a*3 + b              (U_mu[a][b])
+ *      reconstruct-12  24    comp = mu*6 + a*3 + b, a in {0,1}  (row 2 = (row0 x row1)^*)
+ *    QDPG_FERMION      12    comp = s*3 + c
+ *    QDPG_PROPAGATOR  144    comp = (s*3 + c)*12 + (s'*3 + c')  (sink s,c; source s',c')
+ *
+ *  Canonical layout (import/export): complex numbers, site index
+ *  x0 + L0*(x1 + L1*(x2 + L2*x3)); propagator/fermion/colour matrix are
+ *  [site][comp] with the comp order above; the gauge field is
+ *  [mu][site][a][b].
+ */
+#ifndef QDPG_H
+#define QDPG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qdpg_lattice* qdpg_lattice_t; /* opaque, owned by the library */
+typedef struct qdpg_field* qdpg_field_t;     /* opaque header, data borrowed */
+
+typedef enum {
+  QDPG_OK = 0,
+  QDPG_ERR_ARG = -1,         /* null pointer, value out of range */
+  QDPG_ERR_SHAPE = -2,       /* fields on different lattices, wrong kind, buffer too small */
+  QDPG_ERR_DTYPE = -3,       /* precision not valid for this kind or operation */
+  QDPG_ERR_CUDA = -4,        /* a CUDA runtime call or kernel launch failed */
+  QDPG_ERR_NOMEM = -5,       /* a host or device allocation failed */
+  QDPG_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+  QDPG_ERR_UNSUPPORTED = -7  /* valid request this build does not implement */
+} qdpg_status;
+
+typedef enum {
+  QDPG_COLOR_MATRIX = 0,
+  QDPG_GAUGE = 1,
+  QDPG_FERMION = 2,
+  QDPG_PROPAGATOR = 3
+} qdpg_kind;
+
+typedef enum {
+  QDPG_F32 = 0,       /* complex float32 (float2) */
+  QDPG_BF16 = 1,      /* complex bfloat16 pair */
+  QDPG_F32_R12 = 2,   /* gauge only: float2, two rows stored */
+  QDPG_BF16_R12 = 3   /* gauge only: bfloat16 pair, two rows stored */
+} qdpg_prec;
+
+typedef enum {
+  QDPG_CANON_F64 = 0, /* canonical buffer of complex double (2 x double) */
+  QDPG_CANON_F32 = 1  /* canonical buffer of complex float  (2 x float)  */
+} qdpg_canon;
+
+/* Library version, major*10000 + minor*100 + patch. */
+int qdpg_version(void);
+
+/* Number of CUDA kernels this library has launched in this process. */
+uint64_t qdpg_launch_count(void);
+
+/* Copy the calling thread's last error message into buf (always
+ * NUL-terminated when n > 0).  Returns the status of the failed call, or
+ * QDPG_OK if none failed. */
+int qdpg_last_error(char* buf, size_t n);
+
+/* ---- kernel timing ------------------------------------------------------
+ * When enabled, each kernel the library launches is bracketed by two CUDA
+ * events recorded on its own stream.  Kernel names: "smear_hop",
+ * "meson_2pt", "field_import", "field_export", "shift", "point_source".
+ * query() waits for the recorded events and returns the summed elapsed time
+ * (ms) and launch count for one name since the last reset().  At most 65536
+ * launches are recorded per window.  Host-side bookkeeping is thread-safe. */
+int qdpg_profile_enable(int on);
+int qdpg_profile_reset(void);
+int qdpg_profile_query(const char* name, double* total_ms, uint64_t* launches);
+
+/* ---- lattice geometry (paper Sec. 1: QDP++ lattice-wide types) ---------- */
+
+/* Create a lattice of extents dims[4] (each >= 1, product < 2^31, at most
+ * 65535 timeslices) with decay direction j_decay in 0..3.  *out is owned by
+ * the library until qdpg_lattice_destroy.  Host-only; no CUDA call. */
+int qdpg_lattice_create(const int dims[4], int j_decay, qdpg_lattice_t* out);
+void qdpg_lattice_destroy(qdpg_lattice_t lat);
+
+/* Bytes a field of (kind, prec) needs on this lattice (0 if invalid). */
+size_t qdpg_field_bytes(qdpg_lattice_t lat, int kind, int prec);
+
+/* Wrap caller-owned device memory (>= qdpg_field_bytes, 16-byte aligned) as
+ * a field.  No copy, no allocation on the device.  The field keeps its own
+ * copy of the geometry, so it stays valid after the lattice is destroyed. */
+int qdpg_field_wrap(qdpg_lattice_t lat, int kind, int prec, void* dev_ptr, size_t bytes,
+                    qdpg_field_t* out);
+void qdpg_field_release(qdpg_field_t f);
+
+/* ---- field setup (paper Sec. 5: source creation) ------------------------- */
+
+/* Convert a canonical-layout buffer (device memory, element type `canon`)
+ * into `dst`'s device layout and precision.  F32 storage rounds to nearest
+ * even; BF16 rounds to nearest even from the value given; reconstruct-12
+ * keeps rows 0 and 1.  The source must hold V*ncomp complex numbers
+ * (gauge: 4*V*9). */
+int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* stream);
+
+/* Write `src` to a canonical complex-double buffer in device memory
+ * (reconstruct-12 gauge fields are expanded to all nine entries). */
+int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream);
+
+/* Point source at x0 (Sec. 5 "source creation"): zero the field, then set
+ * the unit entries at x0.  PROPAGATOR: all twelve columns,
+ * S[s c][s' c'] = delta_ss' delta_cc'; FERMION: the single entry
+ * spin_color = s*3 + c (0..11).  F32 or BF16 storage. */
+int qdpg_point_source(qdpg_field_t f, const int x0[4], int spin_color, void* stream);
+
+/* ---- shift (QDP++ nearest-neighbour access, Sec. 1) ---------------------- */
+
+/* dst(x) = src(x + sign*mu_hat), periodic; sign = +1 (FORWARD) or -1.
+ * dst and src must be distinct fields of the same kind, precision and
+ * lattice.  Bit-exact copy of elements. */
+int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* stream);
+
+/* ---- Gaussian smearing (Sec. 5: SRC and SNK stages) --------------------- */
+
+/* In-place covariant Gaussian smearing, n_iter iterations of
+ *   psi(x) <- psi(x) + kappa * sum_{i != j_decay} [ U_i(x) psi(x+i)
+ *                                                  + U_i(x-i)^dag psi(x-i) ]
+ * acting on colour; every spin and source column is smeared alike.
+ * U: QDPG_GAUGE (F32, F32_R12, BF16_R12 or BF16); psi: FERMION or
+ * PROPAGATOR (F32 or BF16), same lattice.  Arithmetic is FP32 for every
+ * storage precision.  j_decay selects the direction that is NOT smeared.
+ * scratch: a field of psi's kind/precision/lattice used as the ping-pong
+ * buffer; if NULL the library allocates one stream-ordered
+ * (cudaMallocAsync) and frees it after the last iteration.  n_iter = 0 is a
+ * no-op.  psi and scratch must not alias. */
+int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay,
+                     qdpg_field_t scratch, void* stream);
+
+/* ---- meson two-point functions (Sec. 5: HAD, mesonic) ------------------ */
+
+/* For channels j = 0..n_chan-1 and momenta k = 0..n_mom-1:
+ *   out[j][k][t] = sum_{x: x[j_decay]=t} exp(-i p_k.(x - origin))
+ *                  tr[ Gamma(gamma_snk[j]) S1(x) Gamma(gamma_src[j])^dag
+ *                      gamma_5 S2(x)^dag gamma_5 ]
+ * Gamma(n) = g1^n0 g2^n1 g3^n2 g4^n3 in the DeGrand-Rossi basis (n in 0..15,
+ * Gamma(15) = gamma_5), p_k = 2 pi (moms[3k]/L_a, moms[3k+1]/L_b,
+ * moms[3k+2]/L_c) over the three non-decay directions a < b < c.
+ * S1, S2: PROPAGATOR fields (F32 or BF16) on the same lattice (may be the
+ * same field).  origin: 4 ints or NULL (= 0).
+ * out_dev: device buffer of n_chan*n_mom*Nt complex doubles (2 doubles,
+ * re then im), overwritten.  Site products are FP32; timeslice and momentum
+ * sums are FP64.  Limits: n_chan <= 256, n_mom <= 64. */
+int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src,
+                   int n_chan, const int* moms, int n_mom, const int origin[4], double* out_dev,
+                   void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QDPG_H */

@@ -1,0 +1,250 @@
+"""Python binding of libqdpg: Gaussian smearing and hadron contractions on GB300.
+
+Argument marshalling only: every operation runs in the CUDA kernels of
+libqdpg.so, called through its C ABI (``include/qdpg.h``).  PyTorch provides
+device memory and the current CUDA stream.  There is no CPU fallback: if the
+library is missing, every call raises.
+
+Names follow QDP++/Chroma: a :class:`Lattice` with a decay direction,
+fields of kind GAUGE / PROPAGATOR / FERMION / COLOR_MATRIX, ``shift``,
+``gauss_smear``, ``point_source`` and ``meson_2pt``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libqdpg.so")
+
+COLOR_MATRIX, GAUGE, FERMION, PROPAGATOR = 0, 1, 2, 3
+F32, BF16, F32_R12, BF16_R12 = 0, 1, 2, 3
+CANON_F64, CANON_F32 = 0, 1
+
+PREC_NAMES = {"f32": F32, "bf16": BF16, "f32_r12": F32_R12, "bf16_r12": BF16_R12}
+
+_lib = None
+
+
+class QdpgError(RuntimeError):
+    """A libqdpg call returned a non-zero status."""
+
+    def __init__(self, status: int, message: str):
+        super().__init__(f"qdpg status {status}: {message}")
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    """Load libqdpg.so (built by ``__graft_entry__.build()``); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"libqdpg.so not built ({LIB_PATH}); run __graft_entry__.build() first")
+    lib = ctypes.CDLL(LIB_PATH)
+    vp, i, d, sz = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    ip = ctypes.POINTER(ctypes.c_int)
+    sig = {
+        "qdpg_version": (i, []),
+        "qdpg_launch_count": (ctypes.c_uint64, []),
+        "qdpg_last_error": (i, [ctypes.c_char_p, sz]),
+        "qdpg_lattice_create": (i, [ip, i, ctypes.POINTER(vp)]),
+        "qdpg_lattice_destroy": (None, [vp]),
+        "qdpg_field_bytes": (sz, [vp, i, i]),
+        "qdpg_field_wrap": (i, [vp, i, i, vp, sz, ctypes.POINTER(vp)]),
+        "qdpg_field_release": (None, [vp]),
+        "qdpg_field_import": (i, [vp, vp, i, vp]),
+        "qdpg_field_export": (i, [vp, vp, vp]),
+        "qdpg_point_source": (i, [vp, ip, i, vp]),
+        "qdpg_shift": (i, [vp, vp, i, i, vp]),
+        "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
+        "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
+        "qdpg_profile_enable": (i, [i]),
+        "qdpg_profile_reset": (i, []),
+        "qdpg_profile_query": (i, [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_uint64)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != 0:
+        buf = ctypes.create_string_buffer(512)
+        _lib.qdpg_last_error(buf, 512)
+        raise QdpgError(status, buf.value.decode())
+
+
+def _ints(vals):
+    arr = (ctypes.c_int * len(vals))(*[int(v) for v in vals])
+    return arr
+
+
+def _stream(stream=None):
+    import torch
+
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def launch_count() -> int:
+    """Kernels libqdpg has launched in this process."""
+    return int(load().qdpg_launch_count())
+
+
+def profile_enable(on: bool = True):
+    """Bracket every library kernel launch with CUDA events on its stream."""
+    _check(load().qdpg_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(load().qdpg_profile_reset())
+
+
+def profile_query(name: str) -> tuple[float, int]:
+    """(summed kernel time in ms, launches) of one kernel name since the last reset."""
+    ms = ctypes.c_double()
+    n = ctypes.c_uint64()
+    _check(load().qdpg_profile_query(name.encode(), ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, int(n.value)
+
+
+class Lattice:
+    """Lattice extents ``dims = (L0, L1, L2, L3)`` (x0 fastest) and decay direction."""
+
+    def __init__(self, dims, j_decay: int = 3):
+        lib = load()
+        self.dims = tuple(int(x) for x in dims)
+        self.j_decay = int(j_decay)
+        h = ctypes.c_void_p()
+        _check(lib.qdpg_lattice_create(_ints(self.dims), self.j_decay, ctypes.byref(h)))
+        self._h = h
+
+    @property
+    def Nt(self) -> int:
+        return self.dims[self.j_decay]
+
+    @property
+    def V(self) -> int:
+        return int(np.prod(self.dims))
+
+    @property
+    def V3(self) -> int:
+        return self.V // self.Nt
+
+    def field_bytes(self, kind: int, prec: int) -> int:
+        return int(_lib.qdpg_field_bytes(self._h, kind, prec))
+
+    def canonical_shape(self, kind: int) -> tuple:
+        L0, L1, L2, L3 = self.dims
+        sites = (L3, L2, L1, L0)
+        return {COLOR_MATRIX: sites + (3, 3), GAUGE: (4,) + sites + (3, 3),
+                FERMION: sites + (4, 3), PROPAGATOR: sites + (4, 3, 4, 3)}[kind]
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qdpg_lattice_destroy(self._h)
+            self._h = None
+
+
+class Field:
+    """A lattice-wide field in device layout, backed by a torch CUDA byte tensor."""
+
+    def __init__(self, lattice: Lattice, kind: int, prec: int = F32, device=None, storage=None):
+        import torch
+
+        self.lattice, self.kind, self.prec = lattice, int(kind), int(prec)
+        nbytes = lattice.field_bytes(self.kind, self.prec)
+        if nbytes == 0:
+            raise QdpgError(-3, f"precision {prec} is not valid for kind {kind}")
+        if storage is None:
+            storage = torch.empty(nbytes, dtype=torch.uint8, device=device or "cuda")
+        if storage.numel() * storage.element_size() < nbytes or not storage.is_cuda:
+            raise ValueError("storage must be a CUDA tensor of at least field_bytes bytes")
+        self.storage = storage
+        self.nbytes = nbytes
+        h = ctypes.c_void_p()
+        _check(_lib.qdpg_field_wrap(lattice._h, self.kind, self.prec, ctypes.c_void_p(storage.data_ptr()),
+                                    nbytes, ctypes.byref(h)))
+        self._h = h
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qdpg_field_release(self._h)
+            self._h = None
+
+    def import_(self, canonical, stream=None) -> "Field":
+        """Fill from a canonical-layout complex tensor (complex128 or complex64) on this device."""
+        import torch
+
+        if not isinstance(canonical, torch.Tensor) or not canonical.is_cuda:
+            raise ValueError("canonical data must be a CUDA tensor (copy it with .to('cuda') first)")
+        if tuple(canonical.shape) != self.lattice.canonical_shape(self.kind):
+            raise ValueError(f"canonical shape {tuple(canonical.shape)} != "
+                             f"{self.lattice.canonical_shape(self.kind)}")
+        if canonical.dtype == torch.complex128:
+            ctype = CANON_F64
+        elif canonical.dtype == torch.complex64:
+            ctype = CANON_F32
+        else:
+            raise ValueError("canonical data must be complex128 or complex64")
+        canonical = canonical.contiguous()
+        _check(_lib.qdpg_field_import(self._h, ctypes.c_void_p(canonical.data_ptr()), ctype, _stream(stream)))
+        self._keep = canonical  # stay alive until the stream has consumed it
+        return self
+
+    def export(self, stream=None):
+        """Return the field as a canonical-layout complex128 CUDA tensor."""
+        import torch
+
+        out = torch.empty(self.lattice.canonical_shape(self.kind), dtype=torch.complex128,
+                          device=self.storage.device)
+        _check(_lib.qdpg_field_export(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def like(self) -> "Field":
+        return Field(self.lattice, self.kind, self.prec, device=self.storage.device)
+
+
+def point_source(field: Field, x0=(0, 0, 0, 0), spin_color: int = 0, stream=None) -> Field:
+    _check(_lib.qdpg_point_source(field._h, _ints(x0), int(spin_color), _stream(stream)))
+    return field
+
+
+def shift(dst: Field, src: Field, sign: int, mu: int, stream=None) -> Field:
+    """dst(x) = src(x + sign * mu_hat)."""
+    _check(_lib.qdpg_shift(dst._h, src._h, int(sign), int(mu), _stream(stream)))
+    return dst
+
+
+def gauss_smear(U: Field, psi: Field, kappa: float, n_iter: int, j_decay: int = 3, scratch: Field | None = None,
+                stream=None) -> Field:
+    """In-place Gaussian smearing of ``psi`` (n_iter covariant hops)."""
+    _check(_lib.qdpg_gauss_smear(U._h, psi._h, float(kappa), int(n_iter), int(j_decay),
+                                 scratch._h if scratch is not None else None, _stream(stream)))
+    return psi
+
+
+def meson_2pt(S1: Field, S2: Field, channels, moms=((0, 0, 0),), origin=None, out=None, stream=None):
+    """Meson correlators, complex128 CUDA tensor of shape (n_chan, n_mom, Nt)."""
+    import torch
+
+    channels = list(channels)
+    moms = [tuple(m) for m in moms]
+    nt = S1.lattice.Nt
+    if out is None:
+        out = torch.empty((len(channels), len(moms), nt), dtype=torch.complex128, device=S1.storage.device)
+    flat = [c for m in moms for c in m]
+    _check(_lib.qdpg_meson_2pt(S1._h, S2._h, _ints([c[0] for c in channels]), _ints([c[1] for c in channels]),
+                               len(channels), _ints(flat), len(moms),
+                               _ints(origin) if origin is not None else None,
+                               ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+SIXTEEN_MESONS = tuple((n, n) for n in range(16))

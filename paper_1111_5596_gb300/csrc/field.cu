@@ -1,0 +1,265 @@
+// Field setup kernels: canonical import/export, point source, shift.
+//
+// Source creation is the first stage of the paper's Chroma measurement
+// (Sec. 5); shift is the nearest-neighbour primitive of QDP++ expressions
+// (Sec. 1).  All kernels here are pure data movement.
+#include "qdpg_internal.h"
+#include "qdpg_profile.h"
+
+namespace qdpg {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  const long long cap = 152LL * 32;  // grid-stride beyond 32 CTAs per SM
+  if (b > cap) b = cap;
+  return (int)(b < 1 ? 1 : b);
+}
+
+// ---- element conversion ------------------------------------------------------
+__device__ __forceinline__ void store_elem(float2* p, double re, double im) {
+  *p = make_float2(__double2float_rn(re), __double2float_rn(im));
+}
+__device__ __forceinline__ void store_elem(__nv_bfloat162* p, double re, double im) {
+  __nv_bfloat162 v;
+  v.x = __double2bfloat16(re);
+  v.y = __double2bfloat16(im);
+  *p = v;
+}
+__device__ __forceinline__ void load_elem(const float2* p, double& re, double& im) {
+  float2 v = *p;
+  re = v.x;
+  im = v.y;
+}
+__device__ __forceinline__ void load_elem(const __nv_bfloat162* p, double& re, double& im) {
+  __nv_bfloat162 v = *p;
+  re = __bfloat162float(v.x);
+  im = __bfloat162float(v.y);
+}
+
+// Canonical complex index of device component `comp` at canonical site `site`.
+__device__ __forceinline__ long long canon_index(int kind, bool r12, int nc, long long V, long long site,
+                                                 int comp) {
+  if (kind == QDPG_GAUGE) {
+    int per = r12 ? 6 : 9;
+    int mu = comp / per, e = comp % per;  // rows 0,1 of a reconstruct-12 link keep entry a*3+b
+    return ((long long)mu * V + site) * 9 + e;
+  }
+  return site * nc + comp;
+}
+
+template <typename Src, typename Dst>
+__global__ void __launch_bounds__(kThreads) import_kernel(Dst* __restrict__ dst, const Src* __restrict__ src,
+                                                          Geom g, int kind, bool r12, int nc) {
+  const long long total = g.V * nc;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int s3 = (int)(i % g.V3);
+    long long r = i / g.V3;
+    int comp = (int)(r % nc);
+    int t = (int)(r / nc);
+    long long site = canon_site(g, t, s3);
+    int nc_canon = (kind == QDPG_GAUGE) ? 9 : nc;
+    long long ci = canon_index(kind, r12, nc_canon, g.V, site, comp);
+    store_elem(dst + i, (double)src[2 * ci], (double)src[2 * ci + 1]);
+  }
+}
+
+// Thread per canonical complex entry; reconstructs row 2 of reconstruct-12 links.
+template <typename Dev>
+__global__ void __launch_bounds__(kThreads) export_kernel(double* __restrict__ out, const Dev* __restrict__ dev,
+                                                          Geom g, int kind, bool r12, int nc) {
+  const int nc_canon = (kind == QDPG_GAUGE) ? 9 : nc;
+  const long long nmu = (kind == QDPG_GAUGE) ? 4 : 1;
+  const long long total = nmu * g.V * nc_canon;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int e = (int)(i % nc_canon);
+    long long r = i / nc_canon;
+    long long site = r % g.V;
+    int mu = (int)(r / g.V);
+    // canonical site -> (t, s3)
+    int x[4];
+    long long rr = site;
+    for (int d = 0; d < 4; ++d) {
+      x[d] = (int)(rr % g.L[d]);
+      rr /= g.L[d];
+    }
+    int t = x[g.jd];
+    int s3 = x[g.sd[0]] + g.sL[0] * (x[g.sd[1]] + g.sL[1] * x[g.sd[2]]);
+    const Dev* base = dev + (long long)t * nc * g.V3 + s3;
+    double re, im;
+    if (kind == QDPG_GAUGE && r12) {
+      int a = e / 3, b = e % 3;
+      if (a < 2) {
+        load_elem(base + (long long)(mu * 6 + e) * g.V3, re, im);
+      } else {
+        // row2 = (row0 x row1)^*
+        int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+        double r0r[2], r0i[2], r1r[2], r1i[2];
+        load_elem(base + (long long)(mu * 6 + b1) * g.V3, r0r[0], r0i[0]);
+        load_elem(base + (long long)(mu * 6 + b2) * g.V3, r0r[1], r0i[1]);
+        load_elem(base + (long long)(mu * 6 + 3 + b1) * g.V3, r1r[0], r1i[0]);
+        load_elem(base + (long long)(mu * 6 + 3 + b2) * g.V3, r1r[1], r1i[1]);
+        // c = r0[b1]*r1[b2] - r0[b2]*r1[b1]
+        double cr = (r0r[0] * r1r[1] - r0i[0] * r1i[1]) - (r0r[1] * r1r[0] - r0i[1] * r1i[0]);
+        double ci = (r0r[0] * r1i[1] + r0i[0] * r1r[1]) - (r0r[1] * r1i[0] + r0i[1] * r1r[0]);
+        re = cr;
+        im = -ci;
+      }
+    } else {
+      int comp = (kind == QDPG_GAUGE) ? mu * 9 + e : e;
+      load_elem(base + (long long)comp * g.V3, re, im);
+    }
+    out[2 * i] = re;
+    out[2 * i + 1] = im;
+  }
+}
+
+// Unit entries of a point source; the field was zeroed before.  Element
+// (t, comp, s3) sits at t_off + comp*V3 with t_off = t*ncomp*V3 + s3.
+template <typename Dev>
+__global__ void point_kernel(Dev* __restrict__ f, long long t_off, int V3, int ncomp, int fermion_comp) {
+  const int k = threadIdx.x;
+  if (ncomp == 144) {
+    if (k < 12) store_elem(f + t_off + (long long)(k * 13) * V3, 1.0, 0.0);  // comp (k,k) of the 12x12
+  } else if (k == 0) {
+    store_elem(f + t_off + (long long)fermion_comp * V3, 1.0, 0.0);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads) shift_kernel(T* __restrict__ dst, const T* __restrict__ src, Geom g,
+                                                         int nc, int mu, int sign) {
+  const long long total = g.V * nc;
+  int k = -1;
+  for (int d = 0; d < 3; ++d)
+    if (g.sd[d] == mu) k = d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int s3 = (int)(i % g.V3);
+    long long r = i / g.V3;
+    int comp = (int)(r % nc);
+    int t = (int)(r / nc);
+    int t2 = t, s32 = s3;
+    if (k < 0) {
+      t2 = t + sign;
+      t2 = t2 < 0 ? t2 + g.Nt : (t2 >= g.Nt ? t2 - g.Nt : t2);
+    } else {
+      int c[3];
+      c[0] = s3 % g.sL[0];
+      c[1] = (s3 / g.sL[0]) % g.sL[1];
+      c[2] = s3 / (g.sL[0] * g.sL[1]);
+      int v = c[k] + sign;
+      c[k] = v < 0 ? v + g.sL[k] : (v >= g.sL[k] ? v - g.sL[k] : v);
+      s32 = c[0] + g.sL[0] * (c[1] + g.sL[1] * c[2]);
+    }
+    dst[i] = src[((long long)t2 * nc + comp) * g.V3 + s32];
+  }
+}
+
+}  // namespace
+
+}  // namespace qdpg
+
+using namespace qdpg;
+
+extern "C" {
+
+int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* stream) {
+  if (!dst || !canon_dev) return fail(QDPG_ERR_ARG, "field_import: null argument");
+  if (canon != QDPG_CANON_F64 && canon != QDPG_CANON_F32)
+    return fail(QDPG_ERR_DTYPE, "field_import: canonical type %d unknown", canon);
+  cudaStream_t s = as_stream(stream);
+  const long long total = dst->g.V * dst->ncomp;
+  const bool r12 = is_r12(dst->prec);
+  const int grid = grid_for(total);
+  ProfScope prof("field_import", s);
+  if (is_bf16(dst->prec)) {
+    auto* d = static_cast<__nv_bfloat162*>(dst->data);
+    if (canon == QDPG_CANON_F64)
+      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
+                                                      r12, dst->ncomp);
+    else
+      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
+                                                     r12, dst->ncomp);
+  } else {
+    auto* d = static_cast<float2*>(dst->data);
+    if (canon == QDPG_CANON_F64)
+      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
+                                                      r12, dst->ncomp);
+    else
+      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
+                                                     r12, dst->ncomp);
+  }
+  return check_launch("field_import");
+}
+
+int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream) {
+  if (!src || !canon_dev) return fail(QDPG_ERR_ARG, "field_export: null argument");
+  cudaStream_t s = as_stream(stream);
+  const long long total = (src->kind == QDPG_GAUGE ? 4 * 9 : src->ncomp) * src->g.V;
+  const int grid = grid_for(total);
+  const bool r12 = is_r12(src->prec);
+  ProfScope prof("field_export", s);
+  if (is_bf16(src->prec))
+    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __nv_bfloat162*>(src->data), src->g,
+                                            src->kind, r12, src->ncomp);
+  else
+    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const float2*>(src->data), src->g, src->kind,
+                                            r12, src->ncomp);
+  return check_launch("field_export");
+}
+
+int qdpg_point_source(qdpg_field_t f, const int x0[4], int spin_color, void* stream) {
+  if (!f || !x0) return fail(QDPG_ERR_ARG, "point_source: null argument");
+  if (f->kind != QDPG_PROPAGATOR && f->kind != QDPG_FERMION)
+    return fail(QDPG_ERR_SHAPE, "point_source: field must be a propagator or fermion");
+  if (f->prec != QDPG_F32 && f->prec != QDPG_BF16)
+    return fail(QDPG_ERR_DTYPE, "point_source: storage must be F32 or BF16");
+  for (int mu = 0; mu < 4; ++mu)
+    if (x0[mu] < 0 || x0[mu] >= f->g.L[mu]) return fail(QDPG_ERR_ARG, "point_source: x0[%d] outside lattice", mu);
+  if (f->kind == QDPG_FERMION && (spin_color < 0 || spin_color > 11))
+    return fail(QDPG_ERR_ARG, "point_source: spin_color %d outside 0..11", spin_color);
+  cudaStream_t s = as_stream(stream);
+  const Geom& g = f->g;
+  size_t bytes = (size_t)g.V * f->ncomp * f->esize;
+  cudaError_t e = cudaMemsetAsync(f->data, 0, bytes, s);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "point_source: memset: %s", cudaGetErrorString(e));
+  const int t = x0[g.jd];
+  const int s3 = x0[g.sd[0]] + g.sL[0] * (x0[g.sd[1]] + g.sL[1] * x0[g.sd[2]]);
+  const long long t_off = (long long)t * f->ncomp * g.V3 + s3;
+  const int fc = (f->kind == QDPG_FERMION) ? spin_color : 0;
+  ProfScope prof("point_source", s);
+  if (f->prec == QDPG_BF16)
+    point_kernel<<<1, 32, 0, s>>>(static_cast<__nv_bfloat162*>(f->data), t_off, g.V3, f->ncomp, fc);
+  else
+    point_kernel<<<1, 32, 0, s>>>(static_cast<float2*>(f->data), t_off, g.V3, f->ncomp, fc);
+  return check_launch("point_source");
+}
+
+int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* stream) {
+  if (!dst || !src) return fail(QDPG_ERR_ARG, "shift: null argument");
+  if (sign != 1 && sign != -1) return fail(QDPG_ERR_ARG, "shift: sign must be +1 or -1");
+  if (mu < 0 || mu > 3) return fail(QDPG_ERR_ARG, "shift: mu %d outside 0..3", mu);
+  if (dst->kind != src->kind || dst->prec != src->prec) return fail(QDPG_ERR_SHAPE, "shift: fields differ in kind/precision");
+  for (int d = 0; d < 4; ++d)
+    if (dst->g.L[d] != src->g.L[d] || dst->g.jd != src->g.jd) return fail(QDPG_ERR_SHAPE, "shift: lattices differ");
+  if (dst->data == src->data) return fail(QDPG_ERR_ARG, "shift: dst and src alias");
+  cudaStream_t s = as_stream(stream);
+  const long long total = src->g.V * src->ncomp;
+  const int grid = grid_for(total);
+  ProfScope prof("shift", s);
+  if (src->esize == 8)
+    shift_kernel<<<grid, kThreads, 0, s>>>(static_cast<uint2*>(dst->data), static_cast<const uint2*>(src->data),
+                                           src->g, src->ncomp, mu, sign);
+  else
+    shift_kernel<<<grid, kThreads, 0, s>>>(static_cast<uint32_t*>(dst->data),
+                                           static_cast<const uint32_t*>(src->data), src->g, src->ncomp, mu, sign);
+  return check_launch("shift");
+}
+
+}  // extern "C"

@@ -1,0 +1,363 @@
+// Meson two-point functions: the mesonic part of the paper's hadron-spectrum
+// stage (Sec. 5, Fig. 4 "HAD").
+//
+//   C_j(t, p) = sum_{x in t} exp(-i p.(x - x0))
+//               tr[ Gamma_snk S1(x) Gamma_src^dag g5 S2(x)^dag g5 ]
+//
+// Every DeGrand-Rossi basis element is a signed permutation whose
+// permutation is an XOR with a 2-bit mask (row r has its one nonzero in
+// column r ^ m).  Writing A = Gamma_snk (mask ma) and B = Gamma_src^dag
+// (mask mb), the trace collapses to
+//
+//   c_j(x) = sum_{alpha, beta} w_j(alpha, beta) Q_{ma,mb}(alpha, beta)
+//   Q_{ma,mb}(alpha, beta) = sum_{d, b} S1[alpha d][beta b] conj(S2[(alpha^ma) d][(beta^mb) b])
+//   w_j(alpha, beta) = A[alpha^ma][alpha] B[beta][beta^mb] g5[beta^mb] g5[alpha^ma]
+//
+// so channels that share a mask pair share the 16 colour contractions Q and
+// differ only in the unit-modulus weights w.  The sixteen mesons
+// Gamma_snk = Gamma_src = Gamma(n) use only four mask pairs: 64 colour
+// contractions (576 complex MACs) per site for all sixteen.
+//
+// A thread owns one site.  Site values are FP32; the timeslice/momentum sums
+// are FP64: warp shuffle, then shared memory across warps, then one FP64
+// atomic per block and value.
+#include <vector>
+
+#include "qdpg_internal.h"
+#include "qdpg_profile.h"
+
+namespace qdpg {
+
+namespace {
+
+constexpr int kMesonThreads = 128;
+constexpr int kMaxPassCh = 16;
+constexpr int kMaxMom = 64;
+
+struct MesonPass {
+  int nq;                        // distinct (ma, mb) pairs, 1..4
+  int ma[4], mb[4];
+  int nch;                       // channels, 1..16
+  int q_of[kMaxPassCh];          // pair index of each channel
+  int out_row[kMaxPassCh];       // channel index in the output
+  float2 w[kMaxPassCh][16];      // weight of Q_q[alpha*4 + beta]
+};
+
+struct Moms {
+  int n;
+  int origin[3];                 // origin along the three non-decay directions
+  int k[kMaxMom][3];             // integer momenta
+  bool zero_only;                // single momentum (0,0,0): no phases
+};
+
+__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
+  __nv_bfloat162 v = *p;
+  return __bfloat1622float2(v);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int NQ, typename PsiT>
+__global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __restrict__ S1, const PsiT* __restrict__ S2,
+                                                              Geom g, MesonPass P, Moms M, double* __restrict__ out) {
+  extern __shared__ double2 red[];  // [warp][nch * n_mom]
+  const int s3 = blockIdx.x * kMesonThreads + threadIdx.x;
+  const int t = blockIdx.y;
+  const bool live = s3 < g.V3;
+  const int V3 = g.V3;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nv = P.nch * M.n;
+
+  float2 Q[NQ][16];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int k = 0; k < 16; ++k) Q[q][k] = make_float2(0.f, 0.f);
+
+  if (live) {
+    const long long base = (long long)t * 144 * V3 + s3;
+    const PsiT* p1 = S1 + base;
+    const PsiT* p2 = S2 + base;
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+      for (int be = 0; be < 4; ++be) {
+        float2 a[9];
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) a[d * 3 + b] = ld2(p1 + (long long)((al * 3 + d) * 12 + be * 3 + b) * V3);
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+          const int al2 = al ^ P.ma[q], be2 = be ^ P.mb[q];
+          float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+              const float2 y = ld2(p2 + (long long)((al2 * 3 + d) * 12 + be2 * 3 + b) * V3);
+              const float2 x = a[d * 3 + b];
+              // acc += x * conj(y)
+              acc.x = fmaf(x.x, y.x, acc.x);
+              acc.x = fmaf(x.y, y.y, acc.x);
+              acc.y = fmaf(x.y, y.x, acc.y);
+              acc.y = fmaf(-x.x, y.y, acc.y);
+            }
+          Q[q][al * 4 + be] = acc;
+        }
+      }
+  }
+
+  // exp(-i p.(x - x0)) needs the three non-decay coordinates
+  int c0 = 0, c1 = 0, c2 = 0;
+  if (!M.zero_only && live) {
+    c0 = s3 % g.sL[0];
+    c1 = (s3 / g.sL[0]) % g.sL[1];
+    c2 = s3 / (g.sL[0] * g.sL[1]);
+  }
+
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) {
+    for (int j = 0; j < P.nch; ++j) {
+      if (P.q_of[j] != q) continue;
+      float2 c = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        const float2 w = P.w[j][k];
+        c.x = fmaf(w.x, Q[q][k].x, c.x);
+        c.x = fmaf(-w.y, Q[q][k].y, c.x);
+        c.y = fmaf(w.x, Q[q][k].y, c.y);
+        c.y = fmaf(w.y, Q[q][k].x, c.y);
+      }
+      for (int m = 0; m < M.n; ++m) {
+        float2 v = c;
+        if (!M.zero_only) {
+          // phase index: sum_k n_k (x_k - o_k) V3/L_k  (mod V3), exact in integers
+          long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
+                          (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
+                          (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
+          num %= V3;
+          if (num < 0) num += V3;
+          float sn, cs;
+          sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
+          // v = c * (cs - i sn)
+          v = make_float2(c.x * cs + c.y * sn, c.y * cs - c.x * sn);
+        }
+        double re = live ? (double)v.x : 0.0;
+        double im = live ? (double)v.y : 0.0;
+        re = warp_sum(re);
+        im = warp_sum(im);
+        if (lane == 0) red[warp * nv + j * M.n + m] = make_double2(re, im);
+      }
+    }
+  }
+  __syncthreads();
+  const int nwarps = kMesonThreads / 32;
+  for (int i = threadIdx.x; i < nv; i += kMesonThreads) {
+    double re = 0.0, im = 0.0;
+    for (int w = 0; w < nwarps; ++w) {
+      re += red[w * nv + i].x;
+      im += red[w * nv + i].y;
+    }
+    const int j = i / M.n, m = i % M.n;
+    const long long o = ((long long)P.out_row[j] * M.n + m) * g.Nt + t;
+    atomicAdd(out + 2 * o, re);
+    atomicAdd(out + 2 * o + 1, im);
+  }
+}
+
+// ---- host: DeGrand-Rossi gamma matrices as exact complex integers ----------
+
+struct CInt {
+  int re, im;
+};
+inline CInt operator*(CInt a, CInt b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+inline CInt operator+(CInt a, CInt b) { return {a.re + b.re, a.im + b.im}; }
+inline CInt conj(CInt a) { return {a.re, -a.im}; }
+
+struct Mat4 {
+  CInt m[4][4];
+};
+
+Mat4 mat_mul(const Mat4& a, const Mat4& b) {
+  Mat4 c{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) {
+      CInt s{0, 0};
+      for (int k = 0; k < 4; ++k) s = s + a.m[i][k] * b.m[k][j];
+      c.m[i][j] = s;
+    }
+  return c;
+}
+
+// gamma_1..gamma_4 of the DeGrand-Rossi (QDP++ chiral) basis, listed by the
+// single nonzero of each row: column and value.
+Mat4 basis_gamma(int mu) {
+  static const int col[4][4] = {{3, 2, 1, 0}, {3, 2, 1, 0}, {2, 3, 0, 1}, {2, 3, 0, 1}};
+  static const CInt val[4][4] = {
+      {{0, 1}, {0, 1}, {0, -1}, {0, -1}},   // gamma_1
+      {{-1, 0}, {1, 0}, {1, 0}, {-1, 0}},   // gamma_2
+      {{0, 1}, {0, -1}, {0, -1}, {0, 1}},   // gamma_3
+      {{1, 0}, {1, 0}, {1, 0}, {1, 0}}};    // gamma_4
+  Mat4 g{};
+  for (int r = 0; r < 4; ++r) g.m[r][col[mu][r]] = val[mu][r];
+  return g;
+}
+
+Mat4 Gamma(int n) {
+  Mat4 g{};
+  for (int i = 0; i < 4; ++i) g.m[i][i] = {1, 0};
+  for (int bit = 0; bit < 4; ++bit)
+    if ((n >> bit) & 1) g = mat_mul(g, basis_gamma(bit));
+  return g;
+}
+
+Mat4 dagger(const Mat4& a) {
+  Mat4 c{};
+  for (int i = 0; i < 4; ++i)
+    for (int j = 0; j < 4; ++j) c.m[i][j] = conj(a.m[j][i]);
+  return c;
+}
+
+// XOR mask of a signed permutation (row r -> column r ^ mask); -1 if none.
+int xor_mask(const Mat4& a) {
+  int mask = -1;
+  for (int c = 0; c < 4; ++c)
+    if (a.m[0][c].re || a.m[0][c].im) mask = c;
+  for (int r = 0; r < 4; ++r)
+    for (int c = 0; c < 4; ++c) {
+      bool nz = a.m[r][c].re || a.m[r][c].im;
+      if (nz != (c == (r ^ mask))) return -1;
+    }
+  return mask;
+}
+
+struct Channel {
+  int row, ma, mb;
+  float2 w[16];
+};
+
+int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
+                cudaStream_t s) {
+  const Geom& g = S1->g;
+  dim3 grid((g.V3 + kMesonThreads - 1) / kMesonThreads, g.Nt);
+  const size_t smem = (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
+  const bool bf = S1->prec == QDPG_BF16;
+  ProfScope prof("meson_2pt", s);
+#define QDPG_MESON_LAUNCH(NQ)                                                                                         \
+  do {                                                                                                                \
+    if (bf) {                                                                                                         \
+      auto k = meson_kernel<NQ, __nv_bfloat162>;                                                                      \
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+      k<<<grid, kMesonThreads, smem, s>>>(static_cast<const __nv_bfloat162*>(S1->data),                               \
+                                          static_cast<const __nv_bfloat162*>(S2->data), g, P, M, out);               \
+    } else {                                                                                                          \
+      auto k = meson_kernel<NQ, float2>;                                                                              \
+      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
+      k<<<grid, kMesonThreads, smem, s>>>(static_cast<const float2*>(S1->data), static_cast<const float2*>(S2->data), \
+                                          g, P, M, out);                                                              \
+    }                                                                                                                 \
+  } while (0)
+  switch (P.nq) {
+    case 1: QDPG_MESON_LAUNCH(1); break;
+    case 2: QDPG_MESON_LAUNCH(2); break;
+    case 3: QDPG_MESON_LAUNCH(3); break;
+    default: QDPG_MESON_LAUNCH(4); break;
+  }
+#undef QDPG_MESON_LAUNCH
+  return check_launch("meson_2pt");
+}
+
+}  // namespace
+
+}  // namespace qdpg
+
+using namespace qdpg;
+
+extern "C" {
+
+int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
+                   const int* moms, int n_mom, const int origin[4], double* out_dev, void* stream) {
+  if (!S1 || !S2 || !gamma_snk || !gamma_src || !moms || !out_dev) return fail(QDPG_ERR_ARG, "meson_2pt: null argument");
+  if (S1->kind != QDPG_PROPAGATOR || S2->kind != QDPG_PROPAGATOR)
+    return fail(QDPG_ERR_SHAPE, "meson_2pt: S1 and S2 must be propagators");
+  if ((S1->prec != QDPG_F32 && S1->prec != QDPG_BF16) || S2->prec != S1->prec)
+    return fail(QDPG_ERR_DTYPE, "meson_2pt: S1 and S2 must share F32 or BF16 storage");
+  for (int mu = 0; mu < 4; ++mu)
+    if (S1->g.L[mu] != S2->g.L[mu] || S1->g.jd != S2->g.jd) return fail(QDPG_ERR_SHAPE, "meson_2pt: lattices differ");
+  if (n_chan < 1 || n_chan > 256) return fail(QDPG_ERR_ARG, "meson_2pt: n_chan %d outside 1..256", n_chan);
+  if (n_mom < 1 || n_mom > kMaxMom) return fail(QDPG_ERR_ARG, "meson_2pt: n_mom %d outside 1..%d", n_mom, kMaxMom);
+  const Geom& g = S1->g;
+
+  Moms M{};
+  M.n = n_mom;
+  M.zero_only = (n_mom == 1 && moms[0] == 0 && moms[1] == 0 && moms[2] == 0);
+  for (int k = 0; k < 3; ++k) M.origin[k] = origin ? origin[g.sd[k]] : 0;
+  for (int m = 0; m < n_mom; ++m)
+    for (int k = 0; k < 3; ++k) M.k[m][k] = moms[3 * m + k];
+
+  static const int g5[4] = {1, 1, -1, -1};
+  std::vector<Channel> chans;
+  for (int j = 0; j < n_chan; ++j) {
+    if (gamma_snk[j] < 0 || gamma_snk[j] > 15 || gamma_src[j] < 0 || gamma_src[j] > 15)
+      return fail(QDPG_ERR_ARG, "meson_2pt: gamma index outside 0..15 in channel %d", j);
+    Mat4 A = Gamma(gamma_snk[j]);
+    Mat4 B = dagger(Gamma(gamma_src[j]));
+    Channel c{};
+    c.row = j;
+    c.ma = xor_mask(A);
+    c.mb = xor_mask(B);
+    if (c.ma < 0 || c.mb < 0) return fail(QDPG_ERR_ARG, "meson_2pt: internal gamma table error");
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) {
+        CInt w = A.m[al ^ c.ma][al] * B.m[be][be ^ c.mb];
+        const int sgn = g5[be ^ c.mb] * g5[al ^ c.ma];
+        c.w[al * 4 + be] = make_float2((float)(sgn * w.re), (float)(sgn * w.im));
+      }
+    chans.push_back(c);
+  }
+  // group channels by mask pair, then pack passes of <= 4 pairs and <= 16 channels
+  std::vector<Channel> sorted;
+  for (int pair = 0; pair < 16; ++pair)
+    for (const Channel& c : chans)
+      if (c.ma * 4 + c.mb == pair) sorted.push_back(c);
+
+  cudaStream_t s = as_stream(stream);
+  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)n_chan * n_mom * g.Nt, s);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "meson_2pt: memset: %s", cudaGetErrorString(e));
+
+  MesonPass P{};
+  auto flush = [&]() -> int {
+    if (P.nch == 0) return QDPG_OK;
+    int rc = launch_pass(P, M, S1, S2, out_dev, s);
+    P = MesonPass{};
+    return rc;
+  };
+  for (const Channel& c : sorted) {
+    int q = -1;
+    for (int i = 0; i < P.nq; ++i)
+      if (P.ma[i] == c.ma && P.mb[i] == c.mb) q = i;
+    if ((q < 0 && P.nq == 4) || P.nch == kMaxPassCh) {
+      int rc = flush();
+      if (rc) return rc;
+      q = -1;
+    }
+    if (q < 0) {
+      q = P.nq++;
+      P.ma[q] = c.ma;
+      P.mb[q] = c.mb;
+    }
+    P.q_of[P.nch] = q;
+    P.out_row[P.nch] = c.row;
+    for (int k = 0; k < 16; ++k) P.w[P.nch][k] = c.w[k];
+    ++P.nch;
+  }
+  return flush();
+}
+
+}  // extern "C"

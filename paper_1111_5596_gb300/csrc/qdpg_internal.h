@@ -1,0 +1,73 @@
+// Internal declarations shared by the translation units of libqdpg.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+#include <atomic>
+#include <cstdarg>
+#include <cstddef>
+#include <cstdint>
+
+#include "../../include/qdpg.h"
+
+namespace qdpg {
+
+// Geometry as kernels see it (passed by value).
+struct Geom {
+  int L[4];    // extents per direction
+  int jd;      // decay direction of the storage layout
+  int sd[3];   // the other three directions, increasing
+  int sL[3];   // their extents (s3 = x[sd0] + sL0*(x[sd1] + sL1*x[sd2]))
+  int Nt;      // L[jd]
+  int V3;      // sL0*sL1*sL2
+  long long V; // Nt*V3
+};
+
+}  // namespace qdpg
+
+struct qdpg_lattice {
+  qdpg::Geom g;
+};
+
+struct qdpg_field {
+  qdpg::Geom g;
+  int kind;
+  int prec;
+  int ncomp;     // complex components per site in device storage
+  int esize;     // bytes per complex element
+  void* data;    // borrowed device pointer
+  size_t bytes;  // size of the wrapped buffer
+};
+
+namespace qdpg {
+
+// Error reporting: sets the thread-local message and returns `code`.
+int fail(int code, const char* fmt, ...);
+int ok();
+// Checks cudaGetLastError after a launch; counts the launch.
+int check_launch(const char* what);
+void count_launches(uint64_t n);
+
+int ncomp_of(int kind, int prec);
+int esize_of(int prec);
+bool is_r12(int prec);
+bool is_bf16(int prec);
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Device-side helpers --------------------------------------------------------
+
+// Canonical site index of (t, s3) on geometry g.
+__host__ __device__ inline long long canon_site(const Geom& g, int t, int s3) {
+  int x[4];
+  x[g.jd] = t;
+  int r = s3;
+  x[g.sd[0]] = r % g.sL[0];
+  r /= g.sL[0];
+  x[g.sd[1]] = r % g.sL[1];
+  x[g.sd[2]] = r / g.sL[1];
+  return (long long)x[0] + (long long)g.L[0] * (x[1] + (long long)g.L[1] * (x[2] + (long long)g.L[2] * x[3]));
+}
+
+}  // namespace qdpg

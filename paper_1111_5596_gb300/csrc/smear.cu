@@ -1,0 +1,256 @@
+// Gaussian (Wuppertal) smearing: the paper's SRC and SNK stages (Sec. 5,
+// Fig. 4).  One iteration is the site-fused covariant hop
+//
+//   psi'(x) = psi(x) + kappa * sum_{i != j_decay} [ U_i(x) psi(x+i) + U_i(x-i)^dag psi(x-i) ]
+//
+// on every colour vector of the field (4 spins x 12 source columns for a
+// propagator, 4 spins for a fermion).  A thread owns one site: it loads the
+// six links it needs once (reconstructing row 2 for reconstruct-12 storage)
+// and reuses them for all colour vectors of the site, so link traffic is
+// paid once per site per iteration, not once per column.  Arithmetic is FP32
+// for every storage precision.
+#include "qdpg_internal.h"
+#include "qdpg_profile.h"
+
+namespace qdpg {
+
+namespace {
+
+constexpr int kSmearThreads = 128;
+
+enum LinkMode { L_F32 = 0, L_F32_R12 = 1, L_BF16 = 2, L_BF16_R12 = 3 };
+
+__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
+  __nv_bfloat162 v = *p;
+  return __bfloat1622float2(v);
+}
+__device__ __forceinline__ void st2(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void st2(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
+
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// acc += a * b
+__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+// acc += conj(a) * b
+__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(-a.y, b.x, acc.y);
+}
+
+// Load link U_mu at element offset `off` (= t*ncl*V3 + s3) into m[9].
+template <int LMODE>
+__device__ __forceinline__ void load_link(const void* U, long long off, int V3, int mu, float2 m[9]) {
+  if (LMODE == L_F32 || LMODE == L_BF16) {
+    constexpr int ncl = 36;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      if (LMODE == L_F32)
+        m[e] = ld2(static_cast<const float2*>(U) + off + (long long)(mu * 9 + e) * V3);
+      else
+        m[e] = ld2(static_cast<const __nv_bfloat162*>(U) + off + (long long)(mu * 9 + e) * V3);
+    }
+    (void)ncl;
+  } else {
+#pragma unroll
+    for (int e = 0; e < 6; ++e) {
+      if (LMODE == L_F32_R12)
+        m[e] = ld2(static_cast<const float2*>(U) + off + (long long)(mu * 6 + e) * V3);
+      else
+        m[e] = ld2(static_cast<const __nv_bfloat162*>(U) + off + (long long)(mu * 6 + e) * V3);
+    }
+    // row2[b] = conj(row0[b1] row1[b2] - row0[b2] row1[b1]), (b, b1, b2) cyclic
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+      float2 c = cmul(m[b1], m[3 + b2]);
+      float2 d = cmul(m[b2], m[3 + b1]);
+      m[6 + b] = make_float2(c.x - d.x, -(c.y - d.y));
+    }
+  }
+}
+
+// Neighbour (t2, s3_2) of (t, coords c) one step along direction mu.
+__device__ __forceinline__ void neighbour(const Geom& g, int t, const int c[3], int mu, int sign, int& t2, int& s32) {
+  int cc[3] = {c[0], c[1], c[2]};
+  t2 = t;
+  if (mu == g.jd) {
+    t2 = t + sign;
+    t2 = t2 < 0 ? t2 + g.Nt : (t2 >= g.Nt ? t2 - g.Nt : t2);
+  } else {
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (g.sd[k] == mu) {
+        int v = cc[k] + sign;
+        cc[k] = v < 0 ? v + g.sL[k] : (v >= g.sL[k] ? v - g.sL[k] : v);
+      }
+  }
+  s32 = cc[0] + g.sL[0] * (cc[1] + g.sL[1] * cc[2]);
+}
+
+struct HopDirs {
+  int mu[3];
+};
+
+template <typename PsiT, int LMODE, int COLS>
+__global__ void __launch_bounds__(kSmearThreads) smear_hop_kernel(const PsiT* __restrict__ in, PsiT* __restrict__ out,
+                                                                   const void* __restrict__ U, Geom g, HopDirs hd,
+                                                                   float kappa) {
+  const int s3 = blockIdx.x * kSmearThreads + threadIdx.x;
+  const int t = blockIdx.y;
+  if (s3 >= g.V3) return;
+  constexpr int NC = 12 * COLS;
+  constexpr int NCL = (LMODE == L_F32_R12 || LMODE == L_BF16_R12) ? 24 : 36;
+  const int V3 = g.V3;
+  int c[3];
+  c[0] = s3 % g.sL[0];
+  c[1] = (s3 / g.sL[0]) % g.sL[1];
+  c[2] = s3 / (g.sL[0] * g.sL[1]);
+
+  float2 Uf[3][9], Ub[3][9];
+  long long pf[3], pb[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int mu = hd.mu[i];
+    int tf, sf, tb, sb;
+    neighbour(g, t, c, mu, +1, tf, sf);
+    neighbour(g, t, c, mu, -1, tb, sb);
+    pf[i] = (long long)tf * NC * V3 + sf;
+    pb[i] = (long long)tb * NC * V3 + sb;
+    load_link<LMODE>(U, (long long)t * NCL * V3 + s3, V3, mu, Uf[i]);
+    load_link<LMODE>(U, (long long)tb * NCL * V3 + sb, V3, mu, Ub[i]);
+  }
+  const long long p0 = (long long)t * NC * V3 + s3;
+
+#pragma unroll 1
+  for (int v = 0; v < 4 * COLS; ++v) {
+    const int cb = (v / COLS) * 3 * COLS + (v % COLS);  // comp of colour 0 of this vector
+    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      float2 nf[3], nb[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        nf[k] = ld2(in + pf[i] + (long long)(cb + k * COLS) * V3);
+        nb[k] = ld2(in + pb[i] + (long long)(cb + k * COLS) * V3);
+      }
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          cmac(acc[a], Uf[i][a * 3 + k], nf[k]);       // U_i(x)[a][k] psi(x+i)[k]
+          cmac_conj(acc[a], Ub[i][k * 3 + a], nb[k]);  // conj(U_i(x-i)[k][a]) psi(x-i)[k]
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const long long o = p0 + (long long)(cb + a * COLS) * V3;
+      float2 x = ld2(in + o);
+      x.x = fmaf(kappa, acc[a].x, x.x);
+      x.y = fmaf(kappa, acc[a].y, x.y);
+      st2(out + o, x);
+    }
+  }
+}
+
+template <typename PsiT, int LMODE>
+int launch_hop_cols(const void* in, void* out, const void* U, const Geom& g, HopDirs hd, float kappa, int cols,
+                    cudaStream_t s) {
+  dim3 grid((g.V3 + kSmearThreads - 1) / kSmearThreads, g.Nt);
+  ProfScope prof("smear_hop", s);
+  if (cols == 12)
+    smear_hop_kernel<PsiT, LMODE, 12><<<grid, kSmearThreads, 0, s>>>(static_cast<const PsiT*>(in),
+                                                                    static_cast<PsiT*>(out), U, g, hd, kappa);
+  else
+    smear_hop_kernel<PsiT, LMODE, 1><<<grid, kSmearThreads, 0, s>>>(static_cast<const PsiT*>(in),
+                                                                   static_cast<PsiT*>(out), U, g, hd, kappa);
+  return check_launch("gauss_smear hop");
+}
+
+template <typename PsiT>
+int launch_hop(const void* in, void* out, const void* U, int lprec, const Geom& g, HopDirs hd, float kappa, int cols,
+               cudaStream_t s) {
+  switch (lprec) {
+    case QDPG_F32: return launch_hop_cols<PsiT, L_F32>(in, out, U, g, hd, kappa, cols, s);
+    case QDPG_F32_R12: return launch_hop_cols<PsiT, L_F32_R12>(in, out, U, g, hd, kappa, cols, s);
+    case QDPG_BF16: return launch_hop_cols<PsiT, L_BF16>(in, out, U, g, hd, kappa, cols, s);
+    case QDPG_BF16_R12: return launch_hop_cols<PsiT, L_BF16_R12>(in, out, U, g, hd, kappa, cols, s);
+  }
+  return fail(QDPG_ERR_DTYPE, "gauss_smear: link precision %d", lprec);
+}
+
+bool same_lattice(const Geom& a, const Geom& b) {
+  for (int mu = 0; mu < 4; ++mu)
+    if (a.L[mu] != b.L[mu]) return false;
+  return a.jd == b.jd;
+}
+
+}  // namespace
+
+}  // namespace qdpg
+
+using namespace qdpg;
+
+extern "C" {
+
+int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay, qdpg_field_t scratch,
+                     void* stream) {
+  if (!U || !psi) return fail(QDPG_ERR_ARG, "gauss_smear: null field");
+  if (U->kind != QDPG_GAUGE) return fail(QDPG_ERR_SHAPE, "gauss_smear: U must be a gauge field");
+  if (psi->kind != QDPG_PROPAGATOR && psi->kind != QDPG_FERMION)
+    return fail(QDPG_ERR_SHAPE, "gauss_smear: psi must be a propagator or fermion");
+  if (psi->prec != QDPG_F32 && psi->prec != QDPG_BF16)
+    return fail(QDPG_ERR_DTYPE, "gauss_smear: psi storage must be F32 or BF16");
+  if (!same_lattice(U->g, psi->g)) return fail(QDPG_ERR_SHAPE, "gauss_smear: U and psi on different lattices");
+  if (j_decay < 0 || j_decay > 3) return fail(QDPG_ERR_ARG, "gauss_smear: j_decay %d outside 0..3", j_decay);
+  if (n_iter < 0) return fail(QDPG_ERR_ARG, "gauss_smear: negative iteration count");
+  if (!(kappa == kappa) || kappa > 1e30 || kappa < -1e30) return fail(QDPG_ERR_ARG, "gauss_smear: kappa not finite");
+  if (scratch) {
+    if (scratch->kind != psi->kind || scratch->prec != psi->prec || !same_lattice(scratch->g, psi->g))
+      return fail(QDPG_ERR_SHAPE, "gauss_smear: scratch differs from psi in kind/precision/lattice");
+    if (scratch->data == psi->data) return fail(QDPG_ERR_ARG, "gauss_smear: scratch aliases psi");
+  }
+  if (n_iter == 0) return ok();
+
+  cudaStream_t s = as_stream(stream);
+  const size_t bytes = (size_t)psi->g.V * psi->ncomp * psi->esize;
+  void* tmp = scratch ? scratch->data : nullptr;
+  bool owned = false;
+  if (!tmp) {
+    cudaError_t e = cudaMallocAsync(&tmp, bytes, s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_NOMEM, "gauss_smear: scratch allocation of %zu bytes: %s", bytes,
+                                      cudaGetErrorString(e));
+    owned = true;
+  }
+  HopDirs hd;
+  int k = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    if (mu != j_decay) hd.mu[k++] = mu;
+  const int cols = psi->kind == QDPG_PROPAGATOR ? 12 : 1;
+  void* bufs[2] = {psi->data, tmp};
+  int rc = QDPG_OK;
+  for (int it = 0; it < n_iter && rc == QDPG_OK; ++it) {
+    const void* in = bufs[it & 1];
+    void* out = bufs[(it + 1) & 1];
+    if (psi->prec == QDPG_BF16)
+      rc = launch_hop<__nv_bfloat162>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
+    else
+      rc = launch_hop<float2>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
+  }
+  if (rc == QDPG_OK && (n_iter & 1)) {
+    cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "gauss_smear: copy-back: %s", cudaGetErrorString(e));
+  }
+  if (owned) cudaFreeAsync(tmp, s);
+  return rc;
+}
+
+}  // extern "C"

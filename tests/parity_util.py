@@ -1,0 +1,38 @@
+"""Error norms shared by the GPU parity tests.
+
+Fields: ||a - r||_2 / ||r||_2 over the whole field.  Correlators: per
+(channel, momentum), ||C(.) - C_ref(.)||_2 / ||C_ref(.)||_2 over t; a
+(channel, momentum) whose reference norm is below 1e-12 of the largest one
+is measured against that largest norm instead (it is zero up to rounding).
+"""
+import numpy as np
+
+# FP32 arithmetic on FP32-representable inputs; BF16 storage.
+TOL_F32 = 1e-5
+TOL_BF16 = 2e-2
+
+
+def field_err(a, ref) -> float:
+    a = np.asarray(a)
+    ref = np.asarray(ref)
+    return float(np.linalg.norm((a - ref).ravel()) / np.linalg.norm(ref.ravel()))
+
+
+def corr_err(C, C_ref) -> float:
+    C = np.asarray(C)
+    C_ref = np.asarray(C_ref)
+    diff = np.linalg.norm(C - C_ref, axis=-1)
+    norm = np.linalg.norm(C_ref, axis=-1)
+    floor = 1e-12 * norm.max()
+    denom = np.where(norm > floor, norm, norm.max())
+    return float((diff / denom).max())
+
+
+def to_bf16_complex(a: np.ndarray) -> np.ndarray:
+    """Round real and imaginary parts to bfloat16 (RNE) with torch on the CPU."""
+    import torch
+
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    re = t.real.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    im = t.imag.to(torch.float32).to(torch.bfloat16).to(torch.float64)
+    return torch.complex(re, im).numpy()
