@@ -171,6 +171,25 @@ int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* strea
 int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay,
                      qdpg_field_t scratch, void* stream);
 
+/* Gaussian smearing that allocates nothing.  The paper has no counterpart:
+ * this entry point serves callers that cannot allocate device memory at the
+ * moment they smear -- an application whose own pool manager owns all device
+ * memory, code that must not pay the implicit device synchronisation of
+ * cudaMalloc/cudaFree, or a process whose memory budget is fixed up front.
+ * Same operation, arguments and errors as qdpg_gauss_smear minus `scratch`:
+ * the ping-pong buffer is a static device array owned by the library,
+ * 32 MiB (33554432 bytes), held on every GPU that loads the library until
+ * the process exits.  A psi field larger than that returns QDPG_ERR_ARG
+ * before any launch.  No cudaMalloc, cudaFree or other allocating routine
+ * is called.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the one array and leaves its
+ * contents behind (each call overwrites it before reading it); calls whose
+ * work overlaps on the GPU -- other streams, other host threads -- race on
+ * it, so the caller must serialise them. */
+int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay,
+                             void* stream);
+
 /* ---- meson two-point functions (Sec. 5: HAD, mesonic) ------------------ */
 
 /* For channels j = 0..n_chan-1 and momenta k = 0..n_mom-1:

@@ -60,6 +60,7 @@ def load() -> ctypes.CDLL:
         "qdpg_point_source": (i, [vp, ip, i, vp]),
         "qdpg_shift": (i, [vp, vp, i, i, vp]),
         "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
+        "qdpg_gauss_smear_noalloc": (i, [vp, vp, d, i, i, vp]),
         "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
         "qdpg_profile_enable": (i, [i]),
         "qdpg_profile_reset": (i, []),
@@ -227,6 +228,15 @@ def gauss_smear(U: Field, psi: Field, kappa: float, n_iter: int, j_decay: int = 
     """In-place Gaussian smearing of ``psi`` (n_iter covariant hops)."""
     _check(_lib.qdpg_gauss_smear(U._h, psi._h, float(kappa), int(n_iter), int(j_decay),
                                  scratch._h if scratch is not None else None, _stream(stream)))
+    return psi
+
+
+def gauss_smear_noalloc(U: Field, psi: Field, kappa: float, n_iter: int, j_decay: int = 3, stream=None) -> Field:
+    """Gaussian smearing that allocates nothing: the library's 32 MiB static
+    device scratch serves as the ping-pong buffer, so ``psi`` may be at most
+    that size.  For callers that cannot allocate device memory when they
+    smear.  Calls that overlap on the GPU share the scratch and race."""
+    _check(_lib.qdpg_gauss_smear_noalloc(U._h, psi._h, float(kappa), int(n_iter), int(j_decay), _stream(stream)))
     return psi
 
 

@@ -254,3 +254,93 @@ int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter,
 }
 
 }  // extern "C"
+
+// ---- smearing without any allocation ------------------------------------------
+//
+// Some callers cannot allocate device memory at the point where they smear: a
+// host application whose own pool manager owns all device memory (the way
+// the paper's QDP++ pool serves QUDA's allocations, Sec. 4.3), code that must
+// not pay the implicit device synchronisation of cudaMalloc/cudaFree, or a
+// process whose memory budget is fixed up front.  For them the ping-pong
+// buffer lives in a static device array that the library owns, of fixed size
+// kStaticScratchBytes; every GPU that loads the library holds it until exit.
+
+#include <mutex>
+
+namespace qdpg {
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(32) << 20;  // 32 MiB
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+void* g_static_ptr[kMaxDevices] = {};
+
+// Device address of g_static_scratch on the current device, looked up once
+// per device (the host-side symbol is only a stand-in, not a device address).
+int static_scratch_address(void** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "gauss_smear_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(QDPG_ERR_UNSUPPORTED, "gauss_smear_noalloc: device %d", dev);
+  std::lock_guard<std::mutex> lk(g_static_mu);
+  if (!g_static_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || !p)
+      return fail(QDPG_ERR_CUDA, "gauss_smear_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+    g_static_ptr[dev] = p;
+  }
+  *out = g_static_ptr[dev];
+  return QDPG_OK;
+}
+
+}  // namespace
+}  // namespace qdpg
+
+extern "C" int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay,
+                                        void* stream) {
+  if (!U || !psi) return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: null field");
+  if (U->kind != QDPG_GAUGE) return fail(QDPG_ERR_SHAPE, "gauss_smear_noalloc: U must be a gauge field");
+  if (psi->kind != QDPG_PROPAGATOR && psi->kind != QDPG_FERMION)
+    return fail(QDPG_ERR_SHAPE, "gauss_smear_noalloc: psi must be a propagator or fermion");
+  if (psi->prec != QDPG_F32 && psi->prec != QDPG_BF16)
+    return fail(QDPG_ERR_DTYPE, "gauss_smear_noalloc: psi storage must be F32 or BF16");
+  if (!same_lattice(U->g, psi->g)) return fail(QDPG_ERR_SHAPE, "gauss_smear_noalloc: U and psi on different lattices");
+  if (j_decay < 0 || j_decay > 3) return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: j_decay %d outside 0..3", j_decay);
+  if (n_iter < 0) return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: negative iteration count");
+  if (!(kappa == kappa) || kappa > 1e30 || kappa < -1e30)
+    return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: kappa not finite");
+  const size_t bytes = (size_t)psi->g.V * psi->ncomp * psi->esize;
+  if (bytes > kStaticScratchBytes)
+    return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: field of %zu bytes exceeds the %zu-byte static scratch", bytes,
+                kStaticScratchBytes);
+  if (n_iter == 0) return ok();
+
+  void* tmp = nullptr;
+  int rc = static_scratch_address(&tmp);
+  if (rc) return rc;
+  // The scratch is written in full by the first iteration before it is read,
+  // so stale contents of an earlier call never leak into this one.
+  cudaStream_t s = as_stream(stream);
+  HopDirs hd;
+  int k = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    if (mu != j_decay) hd.mu[k++] = mu;
+  const int cols = psi->kind == QDPG_PROPAGATOR ? 12 : 1;
+  void* bufs[2] = {psi->data, tmp};
+  for (int it = 0; it < n_iter && rc == QDPG_OK; ++it) {
+    const void* in = bufs[it & 1];
+    void* out = bufs[(it + 1) & 1];
+    if (psi->prec == QDPG_BF16)
+      rc = launch_hop<__nv_bfloat162>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
+    else
+      rc = launch_hop<float2>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
+  }
+  if (rc == QDPG_OK && (n_iter & 1)) {
+    cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "gauss_smear_noalloc: copy-back: %s", cudaGetErrorString(e));
+  }
+  return rc;
+}
