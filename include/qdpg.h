@@ -111,6 +111,33 @@ int qdpg_profile_enable(int on);
 int qdpg_profile_reset(void);
 int qdpg_profile_query(const char* name, double* total_ms, uint64_t* launches);
 
+/* ---- device status of bounded waits ---------------------------------------
+ * Pipelined kernels wait on shared-memory barriers with a time limit (1 s by
+ * default).  A wait that runs out does not trap: the kernel records a flag in
+ * a per-device status word, finishes its own in-flight copies and returns.
+ * qdpg_device_status synchronises `stream`, reads and clears that word, and
+ * returns QDPG_ERR_TIMEOUT if any flag was set (QDPG_OK otherwise). */
+int qdpg_device_status(void* stream);
+
+/* Test hooks for the failure path above (host-side settings, process-wide):
+ *  QDPG_DEBUG_WAIT_TIMEOUT_NS  time limit of every bounded wait, 1e3..6e10 ns;
+ *  QDPG_DEBUG_DROP_VECTOR      colour vector (0..47) whose copies the
+ *                              pipelined smearing kernel skips, so that the
+ *                              waits for it run out; -1 (default) = none;
+ *  QDPG_DEBUG_FORCE_SIMPLE_HOP nonzero: always use the one-thread-per-site
+ *                              smearing kernel without the copy pipeline;
+ * and launch-shape settings of the pipelined smearing kernel:
+ *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..256, 0 = default;
+ *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0). */
+enum {
+  QDPG_DEBUG_WAIT_TIMEOUT_NS = 1,
+  QDPG_DEBUG_DROP_VECTOR = 2,
+  QDPG_DEBUG_FORCE_SIMPLE_HOP = 3,
+  QDPG_TUNE_TILE_CONSUMERS = 4,
+  QDPG_TUNE_STAGES = 5
+};
+int qdpg_debug_set(int what, long long value);
+
 /* ---- lattice geometry (paper Sec. 1: QDP++ lattice-wide types) ---------- */
 
 /* Create a lattice of extents dims[4] (each >= 1, product < 2^31, at most

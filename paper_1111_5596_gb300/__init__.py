@@ -62,6 +62,8 @@ def load() -> ctypes.CDLL:
         "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
         "qdpg_gauss_smear_noalloc": (i, [vp, vp, d, i, i, vp]),
         "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
+        "qdpg_device_status": (i, [vp]),
+        "qdpg_debug_set": (i, [i, ctypes.c_longlong]),
         "qdpg_profile_enable": (i, [i]),
         "qdpg_profile_reset": (i, []),
         "qdpg_profile_query": (i, [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_uint64)]),
@@ -96,6 +98,20 @@ def _stream(stream=None):
 def launch_count() -> int:
     """Kernels libqdpg has launched in this process."""
     return int(load().qdpg_launch_count())
+
+
+DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_VECTOR, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
+TUNE_TILE_CONSUMERS, TUNE_STAGES = 4, 5
+
+
+def device_status(stream=None):
+    """Synchronise the stream and raise QdpgError(-6) if a kernel's bounded wait gave up."""
+    _check(load().qdpg_device_status(_stream(stream)))
+
+
+def debug_set(what: int, value: int):
+    """Test hooks: wait time limit (ns), dropped colour vector, forced simple hop kernel."""
+    _check(load().qdpg_debug_set(int(what), int(value)))
 
 
 def profile_enable(on: bool = True):

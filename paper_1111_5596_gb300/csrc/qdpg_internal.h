@@ -9,7 +9,7 @@
 #include <cstddef>
 #include <cstdint>
 
-#include "../../include/qdpg.h"
+#include "qdpg.h"
 
 namespace qdpg {
 
@@ -53,6 +53,22 @@ int ncomp_of(int kind, int prec);
 int esize_of(int prec);
 bool is_r12(int prec);
 bool is_bf16(int prec);
+
+// Per-device status word (device address) for bounded-wait timeouts.
+unsigned int* device_status_word();
+long long wait_timeout_ns();
+int debug_drop_vector();
+bool debug_force_simple_hop();
+int debug_tile_consumers();  // max consumer threads per pipelined tile, 0 = per-geometry default
+int debug_tile_stages();     // pipeline depth, 0 = as many as fit the shared-memory budget
+constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
+constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage
+constexpr unsigned int kStatusDrain = 4u;      // producer gave up draining its own copies
+
+// Pipelined (bulk-copy) smearing hop; returns QDPG_ERR_UNSUPPORTED when the
+// geometry or precision does not fit it, so the caller can use another kernel.
+int launch_hop_tma(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
+                   const int hop_mu[3], float kappa, cudaStream_t s);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -11,72 +11,15 @@
 // for every storage precision.
 #include "qdpg_internal.h"
 #include "qdpg_profile.h"
+#include "smear_common.cuh"
 
 namespace qdpg {
 
 namespace {
 
+using namespace smear_dev;
+
 constexpr int kSmearThreads = 128;
-
-enum LinkMode { L_F32 = 0, L_F32_R12 = 1, L_BF16 = 2, L_BF16_R12 = 3 };
-
-__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
-  __nv_bfloat162 v = *p;
-  return __bfloat1622float2(v);
-}
-__device__ __forceinline__ void st2(float2* p, float2 v) { *p = v; }
-__device__ __forceinline__ void st2(__nv_bfloat162* p, float2 v) { *p = __float22bfloat162_rn(v); }
-
-__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-// acc += a * b
-__device__ __forceinline__ void cmac(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, acc.x);
-  acc.x = fmaf(-a.y, b.y, acc.x);
-  acc.y = fmaf(a.x, b.y, acc.y);
-  acc.y = fmaf(a.y, b.x, acc.y);
-}
-// acc += conj(a) * b
-__device__ __forceinline__ void cmac_conj(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, acc.x);
-  acc.x = fmaf(a.y, b.y, acc.x);
-  acc.y = fmaf(a.x, b.y, acc.y);
-  acc.y = fmaf(-a.y, b.x, acc.y);
-}
-
-// Load link U_mu at element offset `off` (= t*ncl*V3 + s3) into m[9].
-template <int LMODE>
-__device__ __forceinline__ void load_link(const void* U, long long off, int V3, int mu, float2 m[9]) {
-  if (LMODE == L_F32 || LMODE == L_BF16) {
-    constexpr int ncl = 36;
-#pragma unroll
-    for (int e = 0; e < 9; ++e) {
-      if (LMODE == L_F32)
-        m[e] = ld2(static_cast<const float2*>(U) + off + (long long)(mu * 9 + e) * V3);
-      else
-        m[e] = ld2(static_cast<const __nv_bfloat162*>(U) + off + (long long)(mu * 9 + e) * V3);
-    }
-    (void)ncl;
-  } else {
-#pragma unroll
-    for (int e = 0; e < 6; ++e) {
-      if (LMODE == L_F32_R12)
-        m[e] = ld2(static_cast<const float2*>(U) + off + (long long)(mu * 6 + e) * V3);
-      else
-        m[e] = ld2(static_cast<const __nv_bfloat162*>(U) + off + (long long)(mu * 6 + e) * V3);
-    }
-    // row2[b] = conj(row0[b1] row1[b2] - row0[b2] row1[b1]), (b, b1, b2) cyclic
-#pragma unroll
-    for (int b = 0; b < 3; ++b) {
-      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
-      float2 c = cmul(m[b1], m[3 + b2]);
-      float2 d = cmul(m[b2], m[3 + b1]);
-      m[6 + b] = make_float2(c.x - d.x, -(c.y - d.y));
-    }
-  }
-}
 
 // Neighbour (t2, s3_2) of (t, coords c) one step along direction mu.
 __device__ __forceinline__ void neighbour(const Geom& g, int t, const int c[3], int mu, int sign, int& t2, int& s32) {
@@ -129,35 +72,26 @@ __global__ void __launch_bounds__(kSmearThreads) smear_hop_kernel(const PsiT* __
     load_link<LMODE>(U, (long long)tb * NCL * V3 + sb, V3, mu, Ub[i]);
   }
   const long long p0 = (long long)t * NC * V3 + s3;
+  SiteLinks L;
+  make_site_links(Uf, Ub, L);
 
 #pragma unroll 1
   for (int v = 0; v < 4 * COLS; ++v) {
     const int cb = (v / COLS) * 3 * COLS + (v % COLS);  // comp of colour 0 of this vector
-    float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    u64 nf[3][3], nb[3][3];
+    float2 c[3], o[3];
 #pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      float2 nf[3], nb[3];
+    for (int i = 0; i < 3; ++i)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
-        nf[k] = ld2(in + pf[i] + (long long)(cb + k * COLS) * V3);
-        nb[k] = ld2(in + pb[i] + (long long)(cb + k * COLS) * V3);
+        nf[i][k] = pack2(ld2(in + pf[i] + (long long)(cb + k * COLS) * V3));
+        nb[i][k] = pack2(ld2(in + pb[i] + (long long)(cb + k * COLS) * V3));
       }
 #pragma unroll
-      for (int a = 0; a < 3; ++a)
+    for (int a = 0; a < 3; ++a) c[a] = ld2(in + p0 + (long long)(cb + a * COLS) * V3);
+    hop_vector(L, nf, nb, c, kappa, o);
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          cmac(acc[a], Uf[i][a * 3 + k], nf[k]);       // U_i(x)[a][k] psi(x+i)[k]
-          cmac_conj(acc[a], Ub[i][k * 3 + a], nb[k]);  // conj(U_i(x-i)[k][a]) psi(x-i)[k]
-        }
-    }
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-      const long long o = p0 + (long long)(cb + a * COLS) * V3;
-      float2 x = ld2(in + o);
-      x.x = fmaf(kappa, acc[a].x, x.x);
-      x.y = fmaf(kappa, acc[a].y, x.y);
-      st2(out + o, x);
-    }
+    for (int a = 0; a < 3; ++a) st2(out + p0 + (long long)(cb + a * COLS) * V3, o[a]);
   }
 }
 
@@ -178,6 +112,11 @@ int launch_hop_cols(const void* in, void* out, const void* U, const Geom& g, Hop
 template <typename PsiT>
 int launch_hop(const void* in, void* out, const void* U, int lprec, const Geom& g, HopDirs hd, float kappa, int cols,
                cudaStream_t s) {
+  if (!debug_force_simple_hop()) {
+    const int psi_prec = sizeof(PsiT) == 4 ? QDPG_BF16 : QDPG_F32;
+    const int rc = launch_hop_tma(in, out, U, lprec, psi_prec, cols, g, hd.mu, kappa, s);
+    if (rc != QDPG_ERR_UNSUPPORTED) return rc;
+  }
   switch (lprec) {
     case QDPG_F32: return launch_hop_cols<PsiT, L_F32>(in, out, U, g, hd, kappa, cols, s);
     case QDPG_F32_R12: return launch_hop_cols<PsiT, L_F32_R12>(in, out, U, g, hd, kappa, cols, s);

@@ -1,0 +1,92 @@
+// Device-side status word: kernels whose bounded waits give up record it here
+// (never trap), and the host reads it back through qdpg_device_status.
+#include <mutex>
+
+#include "qdpg_internal.h"
+
+namespace qdpg {
+
+namespace {
+
+static __device__ unsigned int g_device_status;
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+unsigned int* g_ptr[kMaxDevices] = {};
+long long g_timeout_ns = 1000000000LL;  // 1 s
+int g_drop_vector = -1;
+bool g_force_simple = false;
+int g_tile_consumers = 0;  // 0: the library's default for the geometry
+int g_tile_stages = 0;
+
+}  // namespace
+
+unsigned int* device_status_word() {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return nullptr;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_device_status) != cudaSuccess) return nullptr;
+    g_ptr[dev] = static_cast<unsigned int*>(p);
+  }
+  return g_ptr[dev];
+}
+
+long long wait_timeout_ns() { return g_timeout_ns; }
+int debug_drop_vector() { return g_drop_vector; }
+bool debug_force_simple_hop() { return g_force_simple; }
+int debug_tile_consumers() { return g_tile_consumers; }
+int debug_tile_stages() { return g_tile_stages; }
+
+}  // namespace qdpg
+
+using namespace qdpg;
+
+extern "C" {
+
+int qdpg_device_status(void* stream) {
+  unsigned int* w = device_status_word();
+  if (!w) return fail(QDPG_ERR_CUDA, "device_status: no status word on this device");
+  cudaStream_t s = as_stream(stream);
+  unsigned int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, w, sizeof(h), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "device_status: %s", cudaGetErrorString(e));
+  if (h) {
+    const unsigned int zero = 0;
+    e = cudaMemcpyAsync(w, &zero, sizeof(zero), cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "device_status: %s", cudaGetErrorString(e));
+    return fail(QDPG_ERR_TIMEOUT, "device_status: a kernel's bounded wait gave up (flags 0x%x)", h);
+  }
+  return ok();
+}
+
+int qdpg_debug_set(int what, long long value) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  switch (what) {
+    case QDPG_DEBUG_WAIT_TIMEOUT_NS:
+      if (value < 1000 || value > 60000000000LL) return fail(QDPG_ERR_ARG, "debug_set: timeout out of range");
+      g_timeout_ns = value;
+      return ok();
+    case QDPG_DEBUG_DROP_VECTOR:
+      g_drop_vector = (int)value;
+      return ok();
+    case QDPG_DEBUG_FORCE_SIMPLE_HOP:
+      g_force_simple = value != 0;
+      return ok();
+    case QDPG_TUNE_TILE_CONSUMERS:
+      if (value != 0 && (value < 32 || value > 256))
+        return fail(QDPG_ERR_ARG, "debug_set: tile consumers outside 32..256 (0 = default)");
+      g_tile_consumers = (int)value;
+      return ok();
+    case QDPG_TUNE_STAGES:
+      if (value != 0 && (value < 2 || value > 16)) return fail(QDPG_ERR_ARG, "debug_set: stages outside 2..16");
+      g_tile_stages = (int)value;
+      return ok();
+  }
+  return fail(QDPG_ERR_ARG, "debug_set: unknown setting %d", what);
+}
+
+}  // extern "C"
