@@ -121,22 +121,45 @@ int qdpg_device_status(void* stream);
 
 /* Test hooks for the failure path above (host-side settings, process-wide):
  *  QDPG_DEBUG_WAIT_TIMEOUT_NS  time limit of every bounded wait, 1e3..6e10 ns;
- *  QDPG_DEBUG_DROP_VECTOR      colour vector (0..47) whose copies the
- *                              pipelined smearing kernel skips, so that the
- *                              waits for it run out; -1 (default) = none;
+ *  QDPG_DEBUG_DROP_STAGE       pipeline stage (counted from 0 within each
+ *                              CTA of the pipelined smearing kernel) whose
+ *                              copies are skipped, so that the waits for it
+ *                              run out; -1 (default) = none;
  *  QDPG_DEBUG_FORCE_SIMPLE_HOP nonzero: always use the one-thread-per-site
  *                              smearing kernel without the copy pipeline;
  * and launch-shape settings of the pipelined smearing kernel:
  *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..256, 0 = default;
- *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0). */
+ *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
+ *  QDPG_TUNE_SPLIT             consumer threads per site, 1 or 2, 0 = default;
+ *  QDPG_TUNE_GRID              0: persistent CTAs (default), 1: one CTA per item. */
 enum {
   QDPG_DEBUG_WAIT_TIMEOUT_NS = 1,
-  QDPG_DEBUG_DROP_VECTOR = 2,
+  QDPG_DEBUG_DROP_STAGE = 2,
   QDPG_DEBUG_FORCE_SIMPLE_HOP = 3,
   QDPG_TUNE_TILE_CONSUMERS = 4,
-  QDPG_TUNE_STAGES = 5
+  QDPG_TUNE_STAGES = 5,
+  QDPG_TUNE_SPLIT = 6,
+  QDPG_TUNE_GRID = 7
 };
 int qdpg_debug_set(int what, long long value);
+
+/* ---- autotuning of the smearing kernel --------------------------------------
+ * The pipelined smearing kernel's tile width and grid (persistent or one CTA
+ * per work item) are picked per (lattice, j_decay, psi precision, link
+ * precision) by measurement.  qdpg_tune_smear times each candidate with
+ * `reps` hops from psi into scratch on `stream` (psi is read, never written;
+ * scratch is overwritten) and stores the fastest in a process-wide table that
+ * later qdpg_gauss_smear calls on such fields use.  It synchronises the host
+ * with the stream.  QDPG_ERR_UNSUPPORTED if the pipelined kernel does not
+ * serve the geometry (then the one-thread-per-site kernel is used anyway).
+ * Explicit QDPG_TUNE_* settings take precedence over the table.
+ * qdpg_tune_query reports the stored choice (sites per tile, grid mode, and
+ * measured microseconds per hop); qdpg_tune_save / qdpg_tune_load write and
+ * read the table as text, one configuration per line. */
+int qdpg_tune_smear(qdpg_field_t U, qdpg_field_t psi, qdpg_field_t scratch, int j_decay, int reps, void* stream);
+int qdpg_tune_query(qdpg_field_t U, qdpg_field_t psi, int* consumers, int* grid_mode, float* us_per_hop);
+int qdpg_tune_save(const char* path);
+int qdpg_tune_load(const char* path);
 
 /* ---- lattice geometry (paper Sec. 1: QDP++ lattice-wide types) ---------- */
 

@@ -64,6 +64,10 @@ def load() -> ctypes.CDLL:
         "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
         "qdpg_device_status": (i, [vp]),
         "qdpg_debug_set": (i, [i, ctypes.c_longlong]),
+        "qdpg_tune_smear": (i, [vp, vp, vp, i, i, vp]),
+        "qdpg_tune_query": (i, [vp, vp, ip, ip, ctypes.POINTER(ctypes.c_float)]),
+        "qdpg_tune_save": (i, [ctypes.c_char_p]),
+        "qdpg_tune_load": (i, [ctypes.c_char_p]),
         "qdpg_profile_enable": (i, [i]),
         "qdpg_profile_reset": (i, []),
         "qdpg_profile_query": (i, [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_uint64)]),
@@ -100,8 +104,8 @@ def launch_count() -> int:
     return int(load().qdpg_launch_count())
 
 
-DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_VECTOR, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
-TUNE_TILE_CONSUMERS, TUNE_STAGES = 4, 5
+DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_STAGE, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
+TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_SPLIT, TUNE_GRID = 4, 5, 6, 7
 
 
 def device_status(stream=None):
@@ -110,7 +114,7 @@ def device_status(stream=None):
 
 
 def debug_set(what: int, value: int):
-    """Test hooks: wait time limit (ns), dropped colour vector, forced simple hop kernel."""
+    """Test hooks: wait time limit (ns), dropped pipeline stage, forced simple hop kernel."""
     _check(load().qdpg_debug_set(int(what), int(value)))
 
 
@@ -254,6 +258,24 @@ def gauss_smear_noalloc(U: Field, psi: Field, kappa: float, n_iter: int, j_decay
     smear.  Calls that overlap on the GPU share the scratch and race."""
     _check(_lib.qdpg_gauss_smear_noalloc(U._h, psi._h, float(kappa), int(n_iter), int(j_decay), _stream(stream)))
     return psi
+
+
+def tune_smear(U: Field, psi: Field, scratch: Field, j_decay: int = 3, reps: int = 5, stream=None):
+    """Time the pipelined smearing kernel's launch shapes on these fields and
+    keep the fastest for later gauss_smear calls; returns (sites per tile,
+    grid mode, microseconds per hop)."""
+    _check(_lib.qdpg_tune_smear(U._h, psi._h, scratch._h, int(j_decay), int(reps), _stream(stream)))
+    c, gm, us = ctypes.c_int(), ctypes.c_int(), ctypes.c_float()
+    _check(_lib.qdpg_tune_query(U._h, psi._h, ctypes.byref(c), ctypes.byref(gm), ctypes.byref(us)))
+    return c.value, gm.value, us.value
+
+
+def tune_save(path: str):
+    _check(load().qdpg_tune_save(path.encode()))
+
+
+def tune_load(path: str):
+    _check(load().qdpg_tune_load(path.encode()))
 
 
 def meson_2pt(S1: Field, S2: Field, channels, moms=((0, 0, 0),), origin=None, out=None, stream=None):

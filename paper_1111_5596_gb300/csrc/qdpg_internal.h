@@ -61,6 +61,8 @@ int debug_drop_vector();
 bool debug_force_simple_hop();
 int debug_tile_consumers();  // max consumer threads per pipelined tile, 0 = per-geometry default
 int debug_tile_stages();     // pipeline depth, 0 = as many as fit the shared-memory budget
+int debug_tile_split();      // consumer threads per site (1 or 2), 0 = default
+int debug_tile_grid();       // 0: persistent CTAs, 1: one CTA per work item
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage
 constexpr unsigned int kStatusDrain = 4u;      // producer gave up draining its own copies

@@ -109,36 +109,47 @@ __device__ __forceinline__ void make_site_links(const float2 Uf[3][9], const flo
       }
 }
 
-// One colour vector of one site: out[a] = c[a] + kappa * sum_i
-//   [ U_i(x) psi(x+i) + U_i(x-i)^dag psi(x-i) ][a]
-// from neighbour values nf[i][q] = psi(x+i)[q], nb[i][q] = psi(x-i)[q].
-__device__ __forceinline__ void hop_vector(const SiteLinks& L, const u64 nf[3][3], const u64 nb[3][3],
-                                           const float2 c[3], float kappa, float2 out[3]) {
+// Half a hop for one colour vector: with M[i] = the site's forward links
+// U_i(x) (or its conjugated backward links conj(U_i(x-i))^T) and n[i][q] the
+// matching neighbour values, h[a] = sum_i (M[i] n[i])[a] as (re, im).
+__device__ __forceinline__ void hop_half(const u64 M[3][9], const u64 n[3][3], float2 h[3]) {
   u64 P[3] = {0ull, 0ull, 0ull}, Q[3] = {0ull, 0ull, 0ull};
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
-    u64 sf[3], sb[3];
+    u64 sw[3];
 #pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      sf[q] = swap2(nf[i][q]);
-      sb[q] = swap2(nb[i][q]);
-    }
+    for (int q = 0; q < 3; ++q) sw[q] = swap2(n[i][q]);
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        P[a] = fma2(L.f[i][a * 3 + q], nf[i][q], P[a]);
-        Q[a] = fma2(L.f[i][a * 3 + q], sf[q], Q[a]);
-        P[a] = fma2(L.b[i][a * 3 + q], nb[i][q], P[a]);
-        Q[a] = fma2(L.b[i][a * 3 + q], sb[q], Q[a]);
+        P[a] = fma2(M[i][a * 3 + q], n[i][q], P[a]);
+        Q[a] = fma2(M[i][a * 3 + q], sw[q], Q[a]);
       }
   }
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float2 p = unpack2(P[a]), qv = unpack2(Q[a]);
-    const float re = p.x - p.y, im = qv.x + qv.y;
-    out[a] = make_float2(fmaf(kappa, re, c[a].x), fmaf(kappa, im, c[a].y));
+    h[a] = make_float2(p.x - p.y, qv.x + qv.y);
   }
+}
+
+// out[a] = c[a] + kappa * (forward half + backward half)[a]; every kernel
+// combines the two halves in this order, so their results agree bit for bit.
+__device__ __forceinline__ float2 hop_combine(float2 c, float2 hf, float2 hb, float kappa) {
+  return make_float2(fmaf(kappa, hf.x + hb.x, c.x), fmaf(kappa, hf.y + hb.y, c.y));
+}
+
+// One colour vector of one site: out[a] = c[a] + kappa * sum_i
+//   [ U_i(x) psi(x+i) + U_i(x-i)^dag psi(x-i) ][a]
+// from neighbour values nf[i][q] = psi(x+i)[q], nb[i][q] = psi(x-i)[q].
+__device__ __forceinline__ void hop_vector(const SiteLinks& L, const u64 nf[3][3], const u64 nb[3][3],
+                                           const float2 c[3], float kappa, float2 out[3]) {
+  float2 hf[3], hb[3];
+  hop_half(L.f, nf, hf);
+  hop_half(L.b, nb, hb);
+#pragma unroll
+  for (int a = 0; a < 3; ++a) out[a] = hop_combine(c[a], hf[a], hb[a], kappa);
 }
 
 }  // namespace smear_dev

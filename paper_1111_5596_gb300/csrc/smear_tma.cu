@@ -1,5 +1,10 @@
 // Dispatcher of the pipelined smearing hop (kernel in smear_tma.cuh): tile
 // choice and the hand-off to the per-precision instantiations.
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "smear_tma.cuh"
 
 namespace qdpg {
@@ -10,26 +15,53 @@ using tma_smear::TmaTile;
 
 constexpr int kG = 2;  // colour vectors per pipeline stage
 
-// Tile of k plane rows: the largest divisor k of Ly with Lx*k <= max_consumers.
-bool pick_tile(const Geom& g, int esize, int max_consumers, int stages, TmaTile& tt) {
+int sm_count() {
+  static int cached[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (!cached[dev]) {
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+    cached[dev] = n;
+  }
+  return cached[dev];
+}
+
+// Tile of k plane rows: the largest divisor k of Ly with Lx*k <= max_consumers;
+// pipeline depth from what shared memory leaves after the link buffer.
+bool pick_tile(const Geom& g, int esize, int link_esize, int link_ne, int max_consumers, int stages, int split,
+               int grid_mode, TmaTile& tt) {
   const int Lx = g.sL[0], Ly = g.sL[1];
-  if ((Lx * esize) % 16 != 0) return false;
+  if ((Lx * esize) % 16 != 0 || (Lx * link_esize) % 16 != 0) return false;
   int best = 0;
   for (int k = 1; k <= Ly; ++k)
     if (Ly % k == 0 && Lx * k <= max_consumers) best = k;
   if (best == 0) return false;
   tt.k = best;
   tt.ntiles_y = Ly / best;
-  tt.cwarps = (Lx * best + 31) / 32;
+  tt.split = split;
+  tt.cwarps = (split * Lx * best + 31) / 32;
   tt.halo = best == Ly ? 0 : 1;
   tt.rowsA = best + 2 * tt.halo;
   tt.rows = tt.rowsA + 2 * best;
   tt.G = kG;
   const size_t stage_bytes = (size_t)kG * 3 * tt.rows * Lx * esize;
-  int S = stages > 0 ? stages : (int)(tma_smear::kSmemBudget / stage_bytes);
+  const size_t link_bytes = (size_t)tma_smear::link_elems(link_ne, best, Lx, tt.halo) * link_esize;
+  // small tiles leave room for two or three CTAs on the SM
+  const int per_sm = tma_smear::ctas_per_sm(Lx * best);
+  const size_t budget = (size_t)(222 / per_sm) * 1024;
+  if (link_bytes + 2 * stage_bytes > budget) return false;
+  int S = stages > 0 ? stages : (int)((budget - link_bytes) / stage_bytes);
   if (S > tma_smear::kMaxStages) S = tma_smear::kMaxStages;
-  if (S < 2 || S * stage_bytes + 16 * S > 227 * 1024) return false;
+  if (S < 2) return false;
   tt.stages = S;
+  tt.smem = (int)(S * stage_bytes + link_bytes + (2 * S + 2) * sizeof(uint64_t));
+  if (tt.smem > 227 * 1024) return false;
+  tt.nitems = tt.ntiles_y * g.sL[2] * g.Nt * tma_smear::kSplit;
+  const int nsm = sm_count();
+  if (nsm <= 0) return false;
+  // persistent: one resident wave of CTAs walks the items; otherwise one CTA per item
+  tt.grid = (grid_mode == 1 || tt.nitems < nsm * per_sm) ? tt.nitems : nsm * per_sm;
   return true;
 }
 
@@ -37,17 +69,61 @@ bool pick_tile(const Geom& g, int esize, int max_consumers, int stages, TmaTile&
 // where smaller CTAs (several per SM) measured faster on GB300.
 int default_consumers(const Geom& g) { return g.sL[0] >= 24 ? 128 : 256; }
 
-}  // namespace
 
-int launch_hop_tma(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
-                   const int hop_mu[3], float kappa, cudaStream_t s) {
-  if (cols != 12) return QDPG_ERR_UNSUPPORTED;
-  for (int i = 0; i < 3; ++i)
-    if (hop_mu[i] != g.sd[i]) return QDPG_ERR_UNSUPPORTED;
+// ---- launch configuration and the autotuning table ---------------------------
+
+struct TileCfg {
+  int consumers;  // most sites per tile
+  int grid_mode;  // 0 persistent, 1 one CTA per item
+  int split;      // consumer threads per site
+  int stages;     // 0: as many as fit
+};
+
+struct TuneKey {
+  int L[4], jd, psi, link;
+  bool operator<(const TuneKey& o) const {
+    return std::tie(L[0], L[1], L[2], L[3], jd, psi, link) <
+           std::tie(o.L[0], o.L[1], o.L[2], o.L[3], o.jd, o.psi, o.link);
+  }
+};
+
+std::mutex g_tune_mu;
+std::map<TuneKey, std::pair<TileCfg, float>> g_tune;  // config and its measured microseconds per hop
+
+TuneKey key_of(const Geom& g, int psi_prec, int lprec) {
+  TuneKey k;
+  for (int mu = 0; mu < 4; ++mu) k.L[mu] = g.L[mu];
+  k.jd = g.jd;
+  k.psi = psi_prec;
+  k.link = lprec;
+  return k;
+}
+
+// The configuration a launch uses: explicit tuning settings first, then the
+// autotuning table, then the defaults.
+TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
+  TileCfg c{debug_tile_consumers(), debug_tile_grid(), debug_tile_split(), debug_tile_stages()};
+  const bool explicit_cfg = c.consumers || c.grid_mode || c.split || c.stages;
+  if (!explicit_cfg) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key_of(g, psi_prec, lprec));
+    if (it != g_tune.end()) return it->second.first;
+  }
+  if (!c.consumers) c.consumers = default_consumers(g);
+  return c;
+}
+
+int launch_hop_tma_cfg(const void* in, void* out, const void* U, int lprec, int psi_prec, const Geom& g, float kappa,
+                       cudaStream_t s, const TileCfg& cfg) {
   const bool bf = psi_prec == QDPG_BF16;
   tma_smear::HopLaunch a;
-  const int cons = debug_tile_consumers() > 0 ? debug_tile_consumers() : default_consumers(g);
-  if (!pick_tile(g, bf ? 4 : 8, cons, debug_tile_stages(), a.tt)) return QDPG_ERR_UNSUPPORTED;
+  const bool lr12 = lprec == QDPG_F32_R12 || lprec == QDPG_BF16_R12;
+  const int lesize = (lprec == QDPG_F32 || lprec == QDPG_F32_R12) ? 8 : 4;
+  // the lane-pair split is instantiated for matching storage/link precisions only
+  const bool matched = bf ? (lprec == QDPG_BF16 || lprec == QDPG_BF16_R12) : (lprec == QDPG_F32 || lprec == QDPG_F32_R12);
+  const int split = matched && cfg.split == 2 ? 2 : 1;
+  if (!pick_tile(g, bf ? 4 : 8, lesize, lr12 ? 6 : 9, cfg.consumers, cfg.stages, split, cfg.grid_mode, a.tt))
+    return QDPG_ERR_UNSUPPORTED;
   a.status = device_status_word();
   if (!a.status) return QDPG_ERR_UNSUPPORTED;
   a.in = in;
@@ -56,9 +132,139 @@ int launch_hop_tma(const void* in, void* out, const void* U, int lprec, int psi_
   a.g = g;
   a.kappa = kappa;
   a.timeout_ns = wait_timeout_ns();
-  a.drop_vec = debug_drop_vector();
+  a.drop_stage = debug_drop_vector();
   a.stream = s;
   return bf ? tma_smear::launch_tma_bf16(lprec, a) : tma_smear::launch_tma_f32(lprec, a);
 }
 
+bool tma_eligible(int cols, const Geom& g, const int hop_mu[3]) {
+  if (cols != 12) return false;
+  for (int i = 0; i < 3; ++i)
+    if (hop_mu[i] != g.sd[i]) return false;
+  return true;
+}
+
+}  // namespace
+
+int launch_hop_tma(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
+                   const int hop_mu[3], float kappa, cudaStream_t s) {
+  if (!tma_eligible(cols, g, hop_mu)) return QDPG_ERR_UNSUPPORTED;
+  return launch_hop_tma_cfg(in, out, U, lprec, psi_prec, g, kappa, s, current_cfg(g, psi_prec, lprec));
+}
+
 }  // namespace qdpg
+
+using namespace qdpg;
+
+extern "C" {
+
+int qdpg_tune_smear(qdpg_field_t U, qdpg_field_t psi, qdpg_field_t scratch, int j_decay, int reps, void* stream) {
+  if (!U || !psi || !scratch) return fail(QDPG_ERR_ARG, "tune_smear: null field");
+  if (U->kind != QDPG_GAUGE || psi->kind != QDPG_PROPAGATOR || scratch->kind != psi->kind ||
+      scratch->prec != psi->prec || scratch->data == psi->data)
+    return fail(QDPG_ERR_SHAPE, "tune_smear: needs a gauge field, a propagator and a distinct scratch propagator");
+  if (reps < 1 || reps > 1000) return fail(QDPG_ERR_ARG, "tune_smear: reps outside 1..1000");
+  const Geom& g = psi->g;
+  int hop_mu[3], k = 0;
+  for (int mu = 0; mu < 4; ++mu)
+    if (mu != j_decay) hop_mu[k++] = mu;
+  if (j_decay < 0 || j_decay > 3 || !tma_eligible(12, g, hop_mu))
+    return fail(QDPG_ERR_UNSUPPORTED, "tune_smear: the pipelined kernel does not serve this geometry");
+  cudaStream_t s = as_stream(stream);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return fail(QDPG_ERR_CUDA, "tune_smear: event creation failed");
+  static const int consumer_opts[] = {256, 192, 128, 96, 64, 48, 32};
+  TileCfg best{0, 0, 1, 0};
+  float best_us = 0.f;
+  int last_k = -1;
+  int rc = QDPG_OK;
+  for (int ci = 0; ci < 7 && rc == QDPG_OK; ++ci) {
+    // skip widths that give the same tile as the previous one
+    int kk = 0;
+    for (int d = 1; d <= g.sL[1]; ++d)
+      if (g.sL[1] % d == 0 && g.sL[0] * d <= consumer_opts[ci]) kk = d;
+    if (kk == 0 || kk == last_k) continue;
+    last_k = kk;
+    for (int gm = 0; gm < 2 && rc == QDPG_OK; ++gm) {
+      const TileCfg cfg{consumer_opts[ci], gm, 1, 0};
+      int r = launch_hop_tma_cfg(psi->data, scratch->data, U->data, U->prec, psi->prec, g, 0.1f, s, cfg);
+      if (r == QDPG_ERR_UNSUPPORTED) continue;
+      if (r != QDPG_OK) { rc = r; break; }
+      cudaEventRecord(e0, s);
+      for (int i = 0; i < reps && r == QDPG_OK; ++i)
+        r = launch_hop_tma_cfg(psi->data, scratch->data, U->data, U->prec, psi->prec, g, 0.1f, s, cfg);
+      cudaEventRecord(e1, s);
+      if (r != QDPG_OK) { rc = r; break; }
+      if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(QDPG_ERR_CUDA, "tune_smear: timing failed"); break; }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const float us = ms * 1e3f / reps;
+      if (best_us == 0.f || us < best_us) {
+        best_us = us;
+        best = cfg;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != QDPG_OK) return rc;
+  if (best_us == 0.f) return fail(QDPG_ERR_UNSUPPORTED, "tune_smear: no configuration ran");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key_of(g, psi->prec, U->prec)] = {best, best_us};
+  return ok();
+}
+
+int qdpg_tune_query(qdpg_field_t U, qdpg_field_t psi, int* consumers, int* grid_mode, float* us_per_hop) {
+  if (!U || !psi || !consumers || !grid_mode || !us_per_hop) return fail(QDPG_ERR_ARG, "tune_query: null argument");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  auto it = g_tune.find(key_of(psi->g, psi->prec, U->prec));
+  if (it == g_tune.end()) return fail(QDPG_ERR_ARG, "tune_query: no tuned configuration for these fields");
+  *consumers = it->second.first.consumers;
+  *grid_mode = it->second.first.grid_mode;
+  *us_per_hop = it->second.second;
+  return ok();
+}
+
+int qdpg_tune_save(const char* path) {
+  if (!path) return fail(QDPG_ERR_ARG, "tune_save: null path");
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(QDPG_ERR_ARG, "tune_save: cannot open %s", path);
+  fprintf(f, "# L0 L1 L2 L3 j_decay psi_prec link_prec consumers grid_mode split stages us_per_hop\n");
+  for (const auto& kv : g_tune) {
+    const TuneKey& k = kv.first;
+    const TileCfg& c = kv.second.first;
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.3f\n", k.L[0], k.L[1], k.L[2], k.L[3], k.jd, k.psi, k.link,
+            c.consumers, c.grid_mode, c.split, c.stages, kv.second.second);
+  }
+  fclose(f);
+  return ok();
+}
+
+int qdpg_tune_load(const char* path) {
+  if (!path) return fail(QDPG_ERR_ARG, "tune_load: null path");
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(QDPG_ERR_ARG, "tune_load: cannot open %s", path);
+  char line[512];
+  int n = 0;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  while (fgets(line, sizeof(line), f)) {
+    if (line[0] == '#') continue;
+    TuneKey k;
+    TileCfg c;
+    float us = 0.f;
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %f", &k.L[0], &k.L[1], &k.L[2], &k.L[3], &k.jd, &k.psi,
+               &k.link, &c.consumers, &c.grid_mode, &c.split, &c.stages, &us) != 12)
+      continue;
+    if (c.consumers < 32 || c.consumers > 256 || c.grid_mode < 0 || c.grid_mode > 1 || c.split < 1 || c.split > 2 ||
+        c.stages < 0 || c.stages > 16)
+      continue;
+    g_tune[k] = {c, us};
+    ++n;
+  }
+  fclose(f);
+  return n > 0 ? ok() : fail(QDPG_ERR_ARG, "tune_load: no valid entries in %s", path);
+}
+
+}  // extern "C"

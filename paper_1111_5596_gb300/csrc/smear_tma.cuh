@@ -1,28 +1,34 @@
-// Pipelined Gaussian-smearing hop (the paper's SRC/SNK stages, Sec. 5):
-// kernel template shared by the per-precision translation units.
+// Pipelined, persistent Gaussian-smearing hop (the paper's SRC/SNK stages,
+// Sec. 5): kernel template shared by the per-precision translation units.
 //
 // Same operation as smear_hop_kernel in smear.cu,
 //   psi'(x) = psi(x) + kappa * sum_{i} [ U_i(x) psi(x+i) + U_i(x-i)^dag psi(x-i) ],
 // organised for GB300's memory system:
 //
-//  * a CTA owns a tile of k rows of one (t, z) plane; each consumer thread
-//    owns one site and keeps its six links in registers for all 48 colour
-//    vectors of the propagator (one link load per site per iteration);
-//  * a producer warp streams, G colour vectors at a time, the three colour
-//    planes of the tile plus its halo (rows y0-1 and y0+k of plane z unless
-//    the tile is the whole plane, and the same k rows of planes z-1 and z+1,
-//    all periodic) from HBM/L2 into shared memory with bulk asynchronous
-//    copies (cp.async.bulk on the TMA engine), several stages ahead of the
-//    consumers, so the bytes in flight per SM do not depend on registers;
-//  * mbarriers hand stages between producer and consumers ("full" with a
-//    transaction count, "empty" with one arrival per consumer warp); every
-//    wait is bounded and a wait that runs out records a flag in the device
-//    status word instead of hanging; the producer then drains its own copies
-//    (bounded as well) before the CTA exits;
+//  * work items are (tile, half of the 48 colour vectors); a tile is k rows
+//    of one (t, z) plane; one CTA per SM (two for tiles of at most 128
+//    sites) walks the items round-robin, so neighbouring planes are in
+//    flight together and share their halo reads in L2;
+//  * each consumer thread owns one site and keeps its six links in registers
+//    for the item's 24 colour vectors;
+//  * one producer warp streams, with bulk asynchronous copies (cp.async.bulk
+//    on the TMA engine), first the links of the item's tile into a
+//    shared-memory link buffer, then G colour vectors per stage of the three
+//    colour planes of the tile plus its halo (rows y0-1 and y0+k of plane z
+//    unless the tile is a whole plane, and the same k rows of planes z-1 and
+//    z+1, all periodic); it runs ahead of the consumers across item
+//    boundaries, so consumers never wait on global loads;
+//  * mbarriers hand stages and the link buffer between producer and
+//    consumers ("full" with a transaction count, "empty" with one arrival per
+//    consumer warp); every wait is bounded, and a wait that runs out records
+//    a flag in the device status word instead of hanging; the producer then
+//    drains its own copies (bounded as well) before the CTA exits;
 //  * for the common tile shapes (LX > 0) the plane width, rows and halo are
 //    template constants, so every shared-memory operand is a register base
 //    plus an immediate offset.
 #pragma once
+
+#include <type_traits>
 
 #include "ptx.cuh"
 #include "qdpg_internal.h"
@@ -36,7 +42,7 @@ using namespace smear_dev;
 
 constexpr int kMaxStages = 16;
 constexpr int kMaxConsumers = 256;
-constexpr size_t kSmemBudget = 200 * 1024;  // bytes of stages per CTA
+constexpr int kSplit = 2;  // work items per tile: colour vectors 0..23 and 24..47
 
 // Shared-memory loads of staged elements (plain loads: __ldg is global-only).
 __device__ __forceinline__ float2 lds(const float2* p) { return *p; }
@@ -45,14 +51,18 @@ __device__ __forceinline__ u64 lds_pair(const float2* p) { return *reinterpret_c
 __device__ __forceinline__ u64 lds_pair(const __nv_bfloat162* p) { return pack2(__bfloat1622float2(*p)); }
 
 struct TmaTile {
-  int k;         // plane rows per tile
-  int ntiles_y;  // Ly / k
-  int cwarps;    // consumer warps
-  int halo;      // 1: rows y0-1 and y0+k are staged; 0: the tile is a whole plane (y wraps inside it)
-  int rowsA;     // rows of plane z per colour: k + 2*halo
-  int rows;      // rows per colour in a stage: rowsA + k (plane z-1) + k (plane z+1)
-  int stages;    // pipeline depth, 2..kMaxStages
-  int G;         // colour vectors per stage
+  int k;          // plane rows per tile
+  int ntiles_y;   // Ly / k
+  int cwarps;     // consumer warps
+  int halo;       // 1: rows y0-1 and y0+k are staged; 0: the tile is a whole plane (y wraps inside it)
+  int rowsA;      // rows of plane z per colour: k + 2*halo
+  int rows;       // rows per colour in a stage: rowsA + k (plane z-1) + k (plane z+1)
+  int stages;     // pipeline depth, 2..kMaxStages
+  int G;          // colour vectors per stage
+  int nitems;     // tiles * kSplit
+  int grid;       // persistent CTAs
+  int smem;       // dynamic shared memory bytes
+  int split;      // consumer threads per site: 1 or 2
 };
 
 struct HopLaunch {
@@ -64,21 +74,87 @@ struct HopLaunch {
   float kappa;
   unsigned int* status;
   long long timeout_ns;
-  int drop_vec;
+  int drop_stage;
   cudaStream_t stream;
 };
 
-template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G>
-__global__ void __launch_bounds__(kMaxConsumers + 32, 1)
+template <int LMODE>
+struct LinkTraits {
+  static constexpr bool r12 = LMODE == L_F32_R12 || LMODE == L_BF16_R12;
+  static constexpr int NE = r12 ? 6 : 9;  // stored entries per link
+  static constexpr bool f32 = LMODE == L_F32 || LMODE == L_F32_R12;
+  typedef typename std::conditional<f32, float2, __nv_bfloat162>::type T;
+};
+
+// Link buffer layout (elements of the link type), for a tile of k rows:
+//   F[i][e][k*Lx]   forward links U_{sd_i}(x), entry e, rows y0..y0+k-1 of plane z
+//   YH[e][Lx]       U_{sd_1} on row y0-1 of plane z (halo tiles only)
+//   ZB[e][k*Lx]     U_{sd_2} on rows y0..y0+k-1 of plane z-1
+__host__ __device__ inline int link_elems(int NE, int k, int Lx, int halo) {
+  return 3 * NE * k * Lx + (halo ? NE * Lx : 0) + NE * k * Lx;
+}
+
+// Read one link (entries at p + e*stride) from the buffer; expand row 2 for
+// reconstruct-12 storage.
+template <int LMODE, typename LT>
+__device__ __forceinline__ void link_from_smem(const LT* p, int stride, float2 m[9]) {
+  constexpr int NE = LinkTraits<LMODE>::NE;
+#pragma unroll
+  for (int e = 0; e < NE; ++e) m[e] = lds(p + e * stride);
+  if (LinkTraits<LMODE>::r12) {
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+      const int b1 = (b + 1) % 3, b2 = (b + 2) % 3;
+      const float2 c = cmul(m[b1], m[3 + b2]);
+      const float2 d = cmul(m[b2], m[3 + b1]);
+      m[6 + b] = make_float2(c.x - d.x, -(c.y - d.y));
+    }
+  }
+}
+
+// Threads per CTA (consumer warps + the producer warp) and the CTAs per SM
+// the register budget is sized for: tiles of at most 128 sites run two CTAs
+// per SM.
+// SPLIT = 1: one consumer thread per site; SPLIT = 2: a lane pair per site
+// (lane l the forward hops, lane l^16 the backward ones), half the link
+// registers per thread and twice the warps.
+template <int LX, int KR, int SPLIT>
+struct TileLaunch {
+  static constexpr int threads = LX ? ((SPLIT * LX * KR + 31) / 32 + 1) * 32 : SPLIT * kMaxConsumers + 32;
+  static constexpr int min_blocks = (LX && LX * KR <= 96) ? 3 : ((LX && LX * KR <= 128) ? 2 : 1);
+};
+
+// CTAs per SM a tile of `sites` sites is sized for (registers and shared memory).
+inline int ctas_per_sm(int sites) { return sites <= 96 ? 3 : (sites <= 128 ? 2 : 1); }
+
+struct ItemPos {
+  int t, z, y0, part;
+};
+
+__device__ __forceinline__ ItemPos decode_item(int it, const TmaTile& tt, int Lz) {
+  const int tile = it / kSplit;
+  ItemPos p;
+  p.part = it % kSplit;
+  p.y0 = (tile % tt.ntiles_y) * tt.k;
+  const int rest = tile / tt.ntiles_y;
+  p.z = rest % Lz;
+  p.t = rest / Lz;
+  return p;
+}
+
+template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G, int SPLIT>
+__global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch<LX, KR, SPLIT>::min_blocks)
     smear_hop_tma_kernel(const PsiT* __restrict__ in, PsiT* __restrict__ out, const void* __restrict__ U, Geom g,
-                         TmaTile tt, float kappa, unsigned int* status, long long timeout_ns, int drop_vec) {
+                         TmaTile tt, float kappa, unsigned int* status, long long timeout_ns, int drop_stage) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
+  typedef typename LinkTraits<LMODE>::T LT;
+  constexpr int NE = LinkTraits<LMODE>::NE;
+  constexpr int NCL = 4 * NE;
   constexpr int COLS = 12;
   constexpr int NC = 12 * COLS;
-  constexpr int NV = 4 * COLS;
-  constexpr int NSTEP = NV / G;
-  static_assert(COLS % G == 0, "G must divide the 12 source columns");
-  constexpr int NCL = (LMODE == L_F32_R12 || LMODE == L_BF16_R12) ? 24 : 36;
+  constexpr int VPI = 4 * COLS / kSplit;  // colour vectors per item
+  constexpr int SPI = VPI / G;            // stages per item
+  static_assert(VPI % G == 0 && COLS % G == 0, "G must divide the vectors of an item and the 12 columns");
   const int Lx = LX ? LX : g.sL[0];
   const int k = LX ? KR : tt.k;
   const int halo = LX ? HALO : tt.halo;
@@ -86,17 +162,21 @@ __global__ void __launch_bounds__(kMaxConsumers + 32, 1)
   const int rows = rowsA + 2 * k;
   const int Ly = g.sL[1], Lz = g.sL[2], V3 = g.V3;
   const int S = tt.stages;
-  const int yb = blockIdx.x % tt.ntiles_y;
-  const int z = blockIdx.x / tt.ntiles_y;
-  const int t = blockIdx.y;
-  const int y0 = yb * k;
-  const int CS = rows * Lx;  // elements per colour region
+  const int kLx = k * Lx;
+  const int CS = rows * Lx;  // elements per colour region of a stage
   const int stage_elems = G * 3 * CS;
   const uint32_t stage_bytes = (uint32_t)stage_elems * sizeof(PsiT);
+  const int lel = link_elems(NE, k, Lx, halo);
+  const uint32_t link_bytes = (uint32_t)lel * sizeof(LT);
+  const int lk_YH = 3 * NE * kLx;
+  const int lk_ZB = lk_YH + (halo ? NE * Lx : 0);
   PsiT* st = reinterpret_cast<PsiT*>(smem_raw);
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * stage_bytes);
+  LT* lbuf = reinterpret_cast<LT*>(smem_raw + (size_t)S * stage_bytes);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + (size_t)S * stage_bytes + link_bytes);
   const uint32_t full0 = ptx::smem_addr(bars);
   const uint32_t empty0 = ptx::smem_addr(bars + S);
+  const uint32_t lfull = ptx::smem_addr(bars + 2 * S);
+  const uint32_t lempty = ptx::smem_addr(bars + 2 * S + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
@@ -104,28 +184,72 @@ __global__ void __launch_bounds__(kMaxConsumers + 32, 1)
       ptx::mbar_init(full0 + 8 * s, 1);
       ptx::mbar_init(empty0 + 8 * s, tt.cwarps);
     }
+    ptx::mbar_init(lfull, 1);
+    ptx::mbar_init(lempty, tt.cwarps);
     ptx::fence_mbar_init();
   }
   __syncthreads();
 
   if (warp == tt.cwarps) {
     // ---------------- producer warp ----------------
-    const PsiT* base_t = in + (size_t)t * NC * V3;
-    const int zm = (z - 1 + Lz) % Lz, zp = (z + 1) % Lz;
-    const int ym = (y0 - 1 + Ly) % Ly, yp = (y0 + k) % Ly;
     const int npieces = halo ? 5 : 3;
     const int ncopies = G * 3 * npieces;
-
-    int j = 0;
-    for (int s = 0, n = 0; j < NSTEP; ++j) {
-      if (n > 0) {
-        const bool ok = ptx::mbar_wait_bounded(empty0 + 8 * s, (n - 1) & 1, timeout_ns);
+    const int nlcopies = 4 * NE + (halo ? NE : 0);
+    int gstage = 0, nitem = 0, last_link = -1;
+    bool failed = false;
+    for (int it = blockIdx.x; it < tt.nitems && !failed; it += gridDim.x, ++nitem) {
+      const ItemPos p = decode_item(it, tt, Lz);
+      const int zm = (p.z - 1 + Lz) % Lz, zp = (p.z + 1) % Lz;
+      const int ym = (p.y0 - 1 + Ly) % Ly, yp = (p.y0 + k) % Ly;
+      // links of the tile, once the consumers hold the previous item's in registers
+      if (nitem > 0) {
+        const bool ok = ptx::mbar_wait_bounded(lempty, (nitem - 1) & 1, timeout_ns);
         if (!__all_sync(0xffffffffu, ok)) {
           if (lane == 0) atomicOr(status, kStatusEmptyWait);
           break;
         }
       }
-      if (j * G > drop_vec || j * G + G <= drop_vec) {  // test hook: skip the stage holding drop_vec
+      if (lane == 0) ptx::mbar_arrive_expect_tx(lfull, link_bytes);
+      __syncwarp();
+      const LT* Ut = static_cast<const LT*>(U) + (size_t)p.t * NCL * V3;
+      for (int cp = lane; cp < nlcopies; cp += 32) {
+        int comp, src_off, dst, n;
+        if (cp < 3 * NE) {  // F[i][e]
+          const int i = cp / NE, e = cp % NE;
+          const int mu = i == 0 ? g.sd[0] : (i == 1 ? g.sd[1] : g.sd[2]);  // no dynamic index into the parameter
+          comp = mu * NE + e;
+          src_off = (p.z * Ly + p.y0) * Lx;
+          dst = (i * NE + e) * kLx;
+          n = kLx;
+        } else if (cp < 4 * NE) {  // ZB[e]
+          const int e = cp - 3 * NE;
+          comp = g.sd[2] * NE + e;
+          src_off = (zm * Ly + p.y0) * Lx;
+          dst = lk_ZB + e * kLx;
+          n = kLx;
+        } else {  // YH[e]
+          const int e = cp - 4 * NE;
+          comp = g.sd[1] * NE + e;
+          src_off = (p.z * Ly + ym) * Lx;
+          dst = lk_YH + e * Lx;
+          n = Lx;
+        }
+        ptx::bulk_g2s(ptx::smem_addr(lbuf + dst), Ut + (size_t)comp * V3 + src_off, (uint32_t)n * sizeof(LT), lfull);
+      }
+      last_link = nitem;
+      // the item's colour vectors, G per stage
+      const PsiT* base_t = in + (size_t)p.t * NC * V3;
+      for (int j = 0; j < SPI; ++j, ++gstage) {
+        const int s = gstage % S, n = gstage / S;
+        if (n > 0) {
+          const bool ok = ptx::mbar_wait_bounded(empty0 + 8 * s, (n - 1) & 1, timeout_ns);
+          if (!__all_sync(0xffffffffu, ok)) {
+            if (lane == 0) atomicOr(status, kStatusEmptyWait);
+            failed = true;
+            break;
+          }
+        }
+        if (gstage == drop_stage) continue;  // test hook: the waits for this stage run out
         if (lane == 0) ptx::mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
         __syncwarp();
         for (int cp = lane; cp < ncopies; cp += 32) {
@@ -134,132 +258,193 @@ __global__ void __launch_bounds__(kMaxConsumers + 32, 1)
           int src_off, dst_row, nrows;
           if (halo) {
             switch (piece) {
-              case 0: src_off = (z * Ly + ym) * Lx; dst_row = 0; nrows = 1; break;
-              case 1: src_off = (z * Ly + y0) * Lx; dst_row = 1; nrows = k; break;
-              case 2: src_off = (z * Ly + yp) * Lx; dst_row = k + 1; nrows = 1; break;
-              case 3: src_off = (zm * Ly + y0) * Lx; dst_row = rowsA; nrows = k; break;
-              default: src_off = (zp * Ly + y0) * Lx; dst_row = rowsA + k; nrows = k; break;
+              case 0: src_off = (p.z * Ly + ym) * Lx; dst_row = 0; nrows = 1; break;
+              case 1: src_off = (p.z * Ly + p.y0) * Lx; dst_row = 1; nrows = k; break;
+              case 2: src_off = (p.z * Ly + yp) * Lx; dst_row = k + 1; nrows = 1; break;
+              case 3: src_off = (zm * Ly + p.y0) * Lx; dst_row = rowsA; nrows = k; break;
+              default: src_off = (zp * Ly + p.y0) * Lx; dst_row = rowsA + k; nrows = k; break;
             }
           } else {
             switch (piece) {
-              case 0: src_off = (z * Ly + y0) * Lx; dst_row = 0; nrows = k; break;
-              case 1: src_off = (zm * Ly + y0) * Lx; dst_row = rowsA; nrows = k; break;
-              default: src_off = (zp * Ly + y0) * Lx; dst_row = rowsA + k; nrows = k; break;
+              case 0: src_off = (p.z * Ly + p.y0) * Lx; dst_row = 0; nrows = k; break;
+              case 1: src_off = (zm * Ly + p.y0) * Lx; dst_row = rowsA; nrows = k; break;
+              default: src_off = (zp * Ly + p.y0) * Lx; dst_row = rowsA + k; nrows = k; break;
             }
           }
-          const int v = j * G + gg;
+          const int v = p.part * VPI + j * G + gg;
           const int comp = (v / COLS) * 3 * COLS + c * COLS + (v % COLS);
           const PsiT* src = base_t + (size_t)comp * V3 + src_off;
           const uint32_t dst = ptx::smem_addr(st + (size_t)s * stage_elems + (gg * 3 + c) * CS + dst_row * Lx);
           ptx::bulk_g2s(dst, src, (uint32_t)(nrows * Lx) * sizeof(PsiT), full0 + 8 * s);
         }
       }
-      if (++s == S) {
-        s = 0;
-        ++n;
-      }
     }
-    // Drain: every copy this warp issued (the last S stages) has landed
-    // before the CTA may exit.
+    // Drain: every copy this warp issued (the last S stages and the last
+    // link fill) has landed before the CTA may exit.
     if (lane == 0) {
-      for (int u = (j > S ? j - S : 0); u < j; ++u)
-        if ((u * G > drop_vec || u * G + G <= drop_vec) &&
-            !ptx::mbar_wait_bounded(full0 + 8 * (u % S), (u / S) & 1, timeout_ns))
+      for (int u = (gstage > S ? gstage - S : 0); u < gstage; ++u)
+        if (u != drop_stage && !ptx::mbar_wait_bounded(full0 + 8 * (u % S), (u / S) & 1, timeout_ns))
           atomicOr(status, kStatusDrain);
+      if (last_link >= 0 && !ptx::mbar_wait_bounded(lfull, last_link & 1, timeout_ns)) atomicOr(status, kStatusDrain);
     }
     return;
   }
 
   // ---------------- consumer warps ----------------
-  const int ctid = threadIdx.x;
-  const bool active = ctid < Lx * k;
-  const int r = active ? ctid / Lx : 0;
-  const int x = active ? ctid % Lx : 0;
-  const int y = y0 + r;
-  const int s3 = x + Lx * (y + Ly * z);
-
-  float2 Uf[3][9], Ub[3][9];
-  if (active) {
-    const int xm = x == 0 ? Lx - 1 : x - 1;
-    const int ymn = y == 0 ? Ly - 1 : y - 1;
-    const int zmn = z == 0 ? Lz - 1 : z - 1;
-    const int sb[3] = {xm + Lx * (y + Ly * z), x + Lx * (ymn + Ly * z), x + Lx * (y + Ly * zmn)};
-    const long long lt = (long long)t * NCL * V3;
-#pragma unroll
-    for (int i = 0; i < 3; ++i) {
-      load_link<LMODE>(U, lt + s3, V3, g.sd[i], Uf[i]);
-      load_link<LMODE>(U, lt + sb[i], V3, g.sd[i], Ub[i]);
-    }
-  }
+  // SPLIT == 1: thread ctid owns site ctid.  SPLIT == 2: warp w covers sites
+  // 16w..16w+15; lanes 0-15 apply the forward hops, lanes 16-31 the backward
+  // hops of the same sites, and the forward lane adds both halves.
+  const int sidx = SPLIT == 1 ? threadIdx.x : (warp * 16 + (lane & 15));
+  const int role = SPLIT == 1 ? 0 : (lane >> 4);  // 0: forward (and the only role when SPLIT == 1)
+  const bool active = sidx < kLx;
+  const int r = active ? sidx / Lx : 0;
+  const int x = active ? sidx % Lx : 0;
+  const int xm = x == 0 ? Lx - 1 : x - 1;
   // shared-memory offsets (elements, within a colour region) of the seven sites
   const int rc = r + halo;
   const int oc = rc * Lx + x;
   const int yp_row = halo ? r + 2 : (r + 1 == k ? 0 : r + 1);
   const int ym_row = halo ? r : (r == 0 ? k - 1 : r - 1);
   const int of[3] = {rc * Lx + (x + 1 == Lx ? 0 : x + 1), yp_row * Lx + x, (rowsA + k + r) * Lx + x};
-  const int ob[3] = {rc * Lx + (x == 0 ? Lx - 1 : x - 1), ym_row * Lx + x, (rowsA + r) * Lx + x};
-  PsiT* outp = out + (size_t)t * NC * V3 + s3;
-  SiteLinks L;
-  make_site_links(Uf, Ub, L);
+  const int ob[3] = {rc * Lx + xm, ym_row * Lx + x, (rowsA + r) * Lx + x};
+  int on[3];  // this lane's neighbours
+#pragma unroll
+  for (int i = 0; i < 3; ++i) on[i] = role ? ob[i] : of[i];
+  // link-buffer offsets of this site's six links
+  const int lf = r * Lx + x;
+  const bool yh = halo && r == 0;
+  const int lyb = yh ? lk_YH + x : NE * kLx + (r == 0 ? k - 1 : r - 1) * Lx + x;
+  const int lyb_stride = yh ? Lx : kLx;
 
-  for (int j = 0, s = 0, n = 0; j < NSTEP; ++j) {
-    const bool ok = ptx::mbar_wait_bounded(full0 + 8 * s, n & 1, timeout_ns);
+  int gstage = 0, nitem = 0;
+  for (int it = blockIdx.x; it < tt.nitems; it += gridDim.x, ++nitem) {
+    const ItemPos p = decode_item(it, tt, Lz);
+    bool ok = ptx::mbar_wait_bounded(lfull, nitem & 1, timeout_ns);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicOr(status, kStatusFullWait);
-      break;
+      return;
     }
+    SiteLinks L;
+    u64 M[3][9];  // SPLIT == 2: this lane's half of the links
     if (active) {
+      if constexpr (SPLIT == 1) {
+        float2 Uf[3][9], Ub[3][9];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) link_from_smem<LMODE>(lbuf + i * NE * kLx + lf, kLx, Uf[i]);
+        link_from_smem<LMODE>(lbuf + r * Lx + xm, kLx, Ub[0]);
+        link_from_smem<LMODE>(lbuf + lyb, lyb_stride, Ub[1]);
+        link_from_smem<LMODE>(lbuf + lk_ZB + lf, kLx, Ub[2]);
+        make_site_links(Uf, Ub, L);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const LT* lp = role == 0 ? lbuf + i * NE * kLx + lf
+                                   : (i == 0 ? lbuf + r * Lx + xm : (i == 1 ? lbuf + lyb : lbuf + lk_ZB + lf));
+          const int lstr = (role == 1 && i == 1) ? lyb_stride : kLx;
+          float2 m[9];
+          link_from_smem<LMODE>(lp, lstr, m);
+#pragma unroll
+          for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+              M[i][a * 3 + q] = role == 0 ? pack2(m[a * 3 + q]) : pack2(m[q * 3 + a].x, -m[q * 3 + a].y);
+        }
+      }
+    }
+    __syncwarp();
+    if (lane == 0) ptx::mbar_arrive(lempty);
+
+    const int s3 = x + Lx * ((p.y0 + r) + Ly * p.z);
+    PsiT* outp = out + (size_t)p.t * NC * V3 + s3;
+    for (int j = 0; j < SPI; ++j, ++gstage) {
+      const int s = gstage % S, n = gstage / S;
+      ok = ptx::mbar_wait_bounded(full0 + 8 * s, n & 1, timeout_ns);
+      if (!__all_sync(0xffffffffu, ok)) {
+        if (lane == 0) atomicOr(status, kStatusFullWait);
+        return;
+      }
       const PsiT* sp = st + (size_t)s * stage_elems;
-      const int v0 = j * G;
+      const int v0 = p.part * VPI + j * G;
       PsiT* po = outp + (size_t)((v0 / COLS) * 3 * COLS + (v0 % COLS)) * V3;
 #pragma unroll
       for (int gg = 0; gg < G; ++gg) {
         const PsiT* sg = sp + gg * 3 * CS;
-        u64 nf[3][3], nb[3][3];
-        float2 c[3], o[3];
+        if constexpr (SPLIT == 1) {
+          if (active) {
+            u64 nf[3][3], nb[3][3];
+            float2 c[3], o[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            nf[i][q] = lds_pair(sg + of[i] + q * CS);
-            nb[i][q] = lds_pair(sg + ob[i] + q * CS);
+              for (int q = 0; q < 3; ++q) {
+                nf[i][q] = lds_pair(sg + of[i] + q * CS);
+                nb[i][q] = lds_pair(sg + ob[i] + q * CS);
+              }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * CS);
+            hop_vector(L, nf, nb, c, kappa, o);
+#pragma unroll
+            for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);
           }
+        } else {
+          float2 h[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+          if (active) {
+            u64 nn[3][3];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * CS);
-        hop_vector(L, nf, nb, c, kappa, o);
+            for (int i = 0; i < 3; ++i)
 #pragma unroll
-        for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);
+              for (int q = 0; q < 3; ++q) nn[i][q] = lds_pair(sg + on[i] + q * CS);
+            hop_half(M, nn, h);
+          }
+          float2 hb[3];
+#pragma unroll
+          for (int a = 0; a < 3; ++a) {
+            hb[a].x = __shfl_xor_sync(0xffffffffu, h[a].x, 16);
+            hb[a].y = __shfl_xor_sync(0xffffffffu, h[a].y, 16);
+          }
+          if (active && role == 0) {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              const float2 c = lds(sg + oc + a * CS);
+              st2(po + (gg + a * COLS) * V3, hop_combine(c, h[a], hb[a], kappa));
+            }
+          }
+        }
       }
-    }
-    __syncwarp();
-    if (lane == 0) ptx::mbar_arrive(empty0 + 8 * s);
-    if (++s == S) {
-      s = 0;
-      ++n;
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(empty0 + 8 * s);
     }
   }
 }
 
-template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G>
+// Shared memory of one CTA: stages, link buffer, barriers.
+template <typename PsiT, typename LT>
+inline size_t tma_smem_bytes(const TmaTile& tt, int Lx, int NE) {
+  const size_t stage_bytes = (size_t)tt.G * 3 * tt.rows * Lx * sizeof(PsiT);
+  const size_t lbytes = (size_t)link_elems(NE, tt.k, Lx, tt.halo) * sizeof(LT);
+  return tt.stages * stage_bytes + lbytes + (2 * tt.stages + 2) * sizeof(uint64_t);
+}
+
+template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G, int SPLIT>
 int launch_tma_t(const HopLaunch& a) {
-  const size_t stage_bytes = (size_t)G * 3 * a.tt.rows * a.g.sL[0] * sizeof(PsiT);
-  const size_t smem = a.tt.stages * stage_bytes + 2 * a.tt.stages * sizeof(uint64_t);
-  auto kern = smear_hop_tma_kernel<PsiT, LMODE, LX, KR, HALO, G>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = smear_hop_tma_kernel<PsiT, LMODE, LX, KR, HALO, G, SPLIT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.tt.smem);
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "gauss_smear: smem attribute: %s", cudaGetErrorString(e));
-  dim3 grid(a.tt.ntiles_y * a.g.sL[2], a.g.Nt);
   dim3 block(32 * (a.tt.cwarps + 1));
   ProfScope prof("smear_hop", a.stream);
-  kern<<<grid, block, smem, a.stream>>>(static_cast<const PsiT*>(a.in), static_cast<PsiT*>(a.out), a.U, a.g, a.tt,
-                                        a.kappa, a.status, a.timeout_ns, a.drop_vec);
+  kern<<<a.tt.grid, block, a.tt.smem, a.stream>>>(static_cast<const PsiT*>(a.in), static_cast<PsiT*>(a.out), a.U,
+                                                  a.g, a.tt, a.kappa, a.status, a.timeout_ns, a.drop_stage);
   return check_launch("gauss_smear hop (pipelined)");
 }
 
 // Tile shapes with compile-time instantiations: (Lx, rows, halo).
 #define QDPG_TMA_FIXED_SHAPES(X) \
   X(16, 16, 0)                   \
+  X(16, 8, 1)                    \
   X(24, 8, 1)                    \
+  X(24, 4, 1)                    \
   X(48, 4, 1)                    \
+  X(48, 2, 1)                    \
   X(8, 8, 0)                     \
   X(12, 12, 0)
 
@@ -269,11 +454,13 @@ template <typename PsiT, int LMODE>
 int launch_tma_any(const HopLaunch& a) {
   const int Lx = a.g.sL[0];
   constexpr int G = 2;
-#define QDPG_TMA_TRY(LXV, KV, HV) \
-  if (Lx == LXV && a.tt.k == KV && a.tt.halo == HV) return launch_tma_t<PsiT, LMODE, LXV, KV, HV, G>(a);
+#define QDPG_TMA_TRY(LXV, KV, HV)                                              \
+  if (Lx == LXV && a.tt.k == KV && a.tt.halo == HV)                            \
+    return a.tt.split == 2 ? launch_tma_t<PsiT, LMODE, LXV, KV, HV, G, 2>(a)   \
+                           : launch_tma_t<PsiT, LMODE, LXV, KV, HV, G, 1>(a);
   QDPG_TMA_FIXED_SHAPES(QDPG_TMA_TRY)
 #undef QDPG_TMA_TRY
-  return launch_tma_t<PsiT, LMODE, 0, 0, 0, G>(a);
+  return a.tt.split == 2 ? launch_tma_t<PsiT, LMODE, 0, 0, 0, G, 2>(a) : launch_tma_t<PsiT, LMODE, 0, 0, 0, G, 1>(a);
 }
 
 int launch_tma_f32(int lprec, const HopLaunch& a);

@@ -40,7 +40,7 @@ def test_pipelined_equals_simple_kernel(qdpg_gpu, dims, prec):
 
 
 def test_pipeline_wait_runs_out_and_reports(qdpg_gpu):
-    """Drop the copies of one colour vector: every wait for it gives up after
+    """Drop the copies of one pipeline stage: every wait for it gives up after
     2 ms, the kernel records the timeout and returns; the context stays usable."""
     q = qdpg_gpu
     dims = (8, 8, 8, 2)
@@ -51,17 +51,39 @@ def test_pipeline_wait_runs_out_and_reports(qdpg_gpu):
     f = _field(q, lat, q.PROPAGATOR, q.F32, psi)
     q.device_status()                                   # clean before
     q.debug_set(q.DEBUG_WAIT_TIMEOUT_NS, 2_000_000)
-    q.debug_set(q.DEBUG_DROP_VECTOR, 5)
+    q.debug_set(q.DEBUG_DROP_STAGE, 5)
     try:
         q.gauss_smear(Uf, f, 0.2, 1, scratch=f.like())
         with pytest.raises(q.QdpgError) as err:
             q.device_status()
         assert err.value.status == -6
     finally:
-        q.debug_set(q.DEBUG_DROP_VECTOR, -1)
+        q.debug_set(q.DEBUG_DROP_STAGE, -1)
         q.debug_set(q.DEBUG_WAIT_TIMEOUT_NS, 1_000_000_000)
     q.device_status()                                   # the flag was cleared
     g = _field(q, lat, q.PROPAGATOR, q.F32, psi)
     q.gauss_smear(Uf, g, 0.2, 2, scratch=g.like())
     q.device_status()
     assert field_err(g.export().cpu().numpy(), smear.gauss_smear(U, psi, 0.2, 2)) <= TOL_F32
+
+
+def test_autotuner_picks_a_config_and_keeps_parity(qdpg_gpu, tmp_path):
+    q = qdpg_gpu
+    dims = (16, 16, 8, 2)
+    lat = q.Lattice(dims, 3)
+    U = fields.round_to_f32(fields.gauge_field(dims, 35, kind="near_unit"))
+    psi = fields.round_to_f32(fields.propagator(dims, 35, envelope=0.3))
+    Uf = _field(q, lat, q.GAUGE, q.F32, U)
+    f = _field(q, lat, q.PROPAGATOR, q.F32, psi)
+    sites, grid_mode, us = q.tune_smear(Uf, f, f.like(), reps=2)
+    assert 32 <= sites <= 256 and grid_mode in (0, 1) and us > 0
+    # psi is only read by the tuner
+    assert np.array_equal(f.export().cpu().numpy(), psi)
+    q.gauss_smear(Uf, f, 0.2, 4, scratch=f.like())
+    q.device_status()
+    assert field_err(f.export().cpu().numpy(), smear.gauss_smear(U, psi, 0.2, 4)) <= TOL_F32
+    path = str(tmp_path / "tune.txt")
+    q.tune_save(path)
+    q.tune_load(path)
+    text = open(path).read()
+    assert f"16 16 8 2 3 {q.F32} {q.F32} {sites} {grid_mode}" in text
