@@ -38,7 +38,7 @@ sys.path.insert(0, ROOT)
 
 METRIC = "smear GB/s (%HBM peak), contraction sites/s; BF16 vs FP32 batched at tol"
 CSRC = os.path.join(ROOT, "paper_1111_5596_gb300", "csrc")
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.txt")
 
 
 def parse_args():
@@ -51,6 +51,8 @@ def parse_args():
                     help="minimum host time of the checker baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="skip the launch-shape autotuning (default shapes; for profiling runs)")
     return ap.parse_args()
 
 
@@ -221,16 +223,20 @@ def measured_peaks() -> dict:
 
 
 def traffic_for(kernel: str):
-    """ncu DRAM bytes per launch, if captured on the current kernel source."""
+    """ncu DRAM bytes per launch, if captured on the current kernel sources."""
     if not os.path.exists(TRAFFIC_FILE):
         return None
     with open(TRAFFIC_FILE) as f:
-        d = json.load(f).get(kernel)
-    if not d:
-        return None
-    with open(os.path.join(CSRC, d["source"]), "rb") as f:
-        sha = hashlib.sha256(f.read()).hexdigest()
-    return d["bytes_per_launch"] if sha == d["source_sha256"] else None
+        for line in f:
+            parts = line.split()
+            if len(parts) != 4 or parts[0] != kernel:
+                continue
+            h = hashlib.sha256()
+            for name in parts[2].split(","):
+                with open(os.path.join(CSRC, name), "rb") as src:
+                    h.update(src.read())
+            return int(parts[1]) if h.hexdigest() == parts[3] else None
+    return None
 
 
 def gpu_arm(args):
@@ -267,7 +273,7 @@ def gpu_arm(args):
     C_h = torch.empty_like(C, device="cpu").pin_memory()
 
     # launch shapes of the smearing kernel, picked by measurement before timing
-    tuned = q.tune_smear(U, snk.import_(P_dev), scratch, w.j_decay, reps=3)
+    tuned = (None, None) if args.no_tune else q.tune_smear(U, snk.import_(P_dev), scratch, w.j_decay, reps=3)
 
     def step_device():
         snk.import_(P_dev)
