@@ -258,6 +258,25 @@ int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const
                    int n_chan, const int* moms, int n_mom, const int origin[4], double* out_dev,
                    void* stream);
 
+/* ---- baryon two-point functions (Sec. 5: HAD, baryonic) ----------------- */
+
+/* For momenta k = 0..n_mom-1:
+ *   out[k][t] = sum_{x: x[j_decay]=t} exp(-i p_k.(x - origin))
+ *               sum_{alpha alpha'} P_{alpha' alpha} < chi_alpha(x) chibar_alpha'(origin) >
+ * with P = (1 + parity * gamma_4)/2 and, for kind 0 (nucleon, uud),
+ * chi = eps_abc (u_a^T C gamma_5 d_b) u_c; for kind 1 (Delta++, uuu),
+ * chi = eps_abc (u_a^T C gamma_3 u_b) u_c; C = gamma_2 gamma_4 and
+ * chibar = eps_a'b'c' ubar_c' (qbar_b' Gbar qbar_a'^T), Gbar = g4 G^dag g4
+ * (DeGrand-Rossi basis).  Every Wick pairing enters with the sign of the
+ * Grassmann reordering; the fully nested pairing has sign +1.  Su, Sd:
+ * point-to-all PROPAGATOR fields (F32 or BF16, same lattice); Sd is used by
+ * the nucleon only and may be NULL for the Delta.  origin: 4 ints or NULL;
+ * momenta as in qdpg_meson_2pt.  out_dev: device buffer of n_mom*Nt
+ * complex doubles, overwritten.  Site values FP32, sums FP64.
+ * Limits: n_mom <= 64. */
+int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const int* moms, int n_mom,
+                    const int origin[4], double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

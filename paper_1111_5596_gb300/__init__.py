@@ -62,6 +62,7 @@ def load() -> ctypes.CDLL:
         "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
         "qdpg_gauss_smear_noalloc": (i, [vp, vp, d, i, i, vp]),
         "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
+        "qdpg_baryon_2pt": (i, [vp, vp, i, i, ip, i, ip, vp, vp]),
         "qdpg_device_status": (i, [vp]),
         "qdpg_debug_set": (i, [i, ctypes.c_longlong]),
         "qdpg_tune_smear": (i, [vp, vp, vp, i, i, vp]),
@@ -292,6 +293,24 @@ def meson_2pt(S1: Field, S2: Field, channels, moms=((0, 0, 0),), origin=None, ou
                                len(channels), _ints(flat), len(moms),
                                _ints(origin) if origin is not None else None,
                                ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+NUCLEON, DELTA = 0, 1
+
+
+def baryon_2pt(Su: Field, Sd: Field | None = None, kind: int = NUCLEON, parity: int = +1, moms=((0, 0, 0),),
+               origin=None, out=None, stream=None):
+    """Nucleon (kind 0, uud) or Delta++ (kind 1, uuu) correlator, complex128 CUDA tensor (n_mom, Nt)."""
+    import torch
+
+    moms = [tuple(m) for m in moms]
+    if out is None:
+        out = torch.empty((len(moms), Su.lattice.Nt), dtype=torch.complex128, device=Su.storage.device)
+    flat = [c for m in moms for c in m]
+    _check(_lib.qdpg_baryon_2pt(Su._h, Sd._h if Sd is not None else None, int(kind), int(parity), _ints(flat),
+                                len(moms), _ints(origin) if origin is not None else None,
+                                ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 

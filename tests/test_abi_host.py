@@ -145,6 +145,13 @@ def test_operation_argument_errors_are_caught_on_host(q):
     assert m(P, P, g, g, 0, mom, 1, None, out, None) == ERR_ARG
     assert m(P, P, g, g, 1, mom, 65, None, out, None) == ERR_ARG
     assert m(P, P, g, g, 1, mom, 1, None, None, None) == ERR_ARG
+    b = L.qdpg_baryon_2pt
+    assert b(P, P, 2, 1, mom, 1, None, out, None) == ERR_ARG          # kind
+    assert b(P, P, 0, 0, mom, 1, None, out, None) == ERR_ARG          # parity
+    assert b(P, None, 0, 1, mom, 1, None, out, None) == ERR_ARG       # nucleon needs Sd
+    assert b(P, F, 0, 1, mom, 1, None, out, None) == ERR_SHAPE
+    assert b(P, P2, 0, 1, mom, 1, None, out, None) == ERR_SHAPE
+    assert b(P, P, 1, 1, mom, 65, None, out, None) == ERR_ARG
     assert L.qdpg_field_import(P, None, 0, None) == ERR_ARG
     assert L.qdpg_field_import(P, out, 7, None) == ERR_DTYPE
     assert q.launch_count() == launches_before                    # every error came before a launch
