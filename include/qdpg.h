@@ -277,6 +277,30 @@ int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const
 int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const int* moms, int n_mom,
                     const int origin[4], double* out_dev, void* stream);
 
+/* ---- site values and momentum projection on the tensor cores ------------- */
+
+/* Site values instead of sums: sites_dev (device, 8-byte aligned) receives
+ * complex floats sites[j][t][x3] = the channel-j site trace of
+ * qdpg_meson_2pt at the site (t, x3) (device layout order), n_chan*Nt*V3
+ * of them. */
+int qdpg_meson_sites(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
+                     void* sites_dev, void* stream);
+
+/* As qdpg_baryon_2pt, but writes the site values sites[t][x3] (Nt*V3
+ * complex floats) instead of projecting. */
+int qdpg_baryon_sites(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, void* sites_dev, void* stream);
+
+/* Momentum projection of site values (the dense part of the hadron stage):
+ *   out[j][k][t] = sum_{x3} sites[j][t][x3] exp(-i p_k.(x - origin))
+ * with sites as written by qdpg_meson_sites / qdpg_baryon_sites on lattice
+ * `lat` (n_chan blocks of Nt*V3 complex floats, device memory) and p_k, origin
+ * as in qdpg_meson_2pt.  Computed as a complex GEMM on the 5th-generation
+ * tensor cores (tcgen05, TF32 with hi/lo operand splitting, FP32
+ * accumulation per CTA, FP64 sums across CTAs).  out_dev: device buffer of
+ * n_chan*n_mom*Nt complex doubles, overwritten.  Limits: n_mom <= 64. */
+int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, int n_chan, const int* moms, int n_mom,
+                          const int origin[4], double* out_dev, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -63,6 +63,9 @@ def load() -> ctypes.CDLL:
         "qdpg_gauss_smear_noalloc": (i, [vp, vp, d, i, i, vp]),
         "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
         "qdpg_baryon_2pt": (i, [vp, vp, i, i, ip, i, ip, vp, vp]),
+        "qdpg_meson_sites": (i, [vp, vp, ip, ip, i, vp, vp]),
+        "qdpg_baryon_sites": (i, [vp, vp, i, i, vp, vp]),
+        "qdpg_momentum_project": (i, [vp, vp, i, ip, i, ip, vp, vp]),
         "qdpg_device_status": (i, [vp]),
         "qdpg_debug_set": (i, [i, ctypes.c_longlong]),
         "qdpg_tune_smear": (i, [vp, vp, vp, i, i, vp]),
@@ -312,6 +315,58 @@ def baryon_2pt(Su: Field, Sd: Field | None = None, kind: int = NUCLEON, parity: 
                                 len(moms), _ints(origin) if origin is not None else None,
                                 ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
+
+
+def meson_sites(S1: Field, S2: Field, channels, out=None, stream=None):
+    """Site traces of the meson channels, complex64 CUDA tensor (n_chan, Nt, V3)."""
+    import torch
+
+    channels = list(channels)
+    lat = S1.lattice
+    if out is None:
+        out = torch.empty((len(channels), lat.Nt, lat.V3), dtype=torch.complex64, device=S1.storage.device)
+    _check(_lib.qdpg_meson_sites(S1._h, S2._h, _ints([c[0] for c in channels]), _ints([c[1] for c in channels]),
+                                 len(channels), ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def baryon_sites(Su: Field, Sd: Field | None = None, kind: int = NUCLEON, parity: int = +1, out=None, stream=None):
+    """Baryon site values, complex64 CUDA tensor (Nt, V3)."""
+    import torch
+
+    lat = Su.lattice
+    if out is None:
+        out = torch.empty((lat.Nt, lat.V3), dtype=torch.complex64, device=Su.storage.device)
+    _check(_lib.qdpg_baryon_sites(Su._h, Sd._h if Sd is not None else None, int(kind), int(parity),
+                                  ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def momentum_project(lattice: Lattice, sites, moms, origin=None, out=None, stream=None):
+    """Project site values (n_chan, Nt, V3) complex64 onto momenta on the tensor
+    cores; complex128 CUDA tensor (n_chan, n_mom, Nt)."""
+    import torch
+
+    if sites.dtype != torch.complex64 or not sites.is_cuda or not sites.is_contiguous():
+        raise ValueError("sites must be a contiguous complex64 CUDA tensor")
+    n_chan = sites.numel() // (lattice.Nt * lattice.V3)
+    if n_chan * lattice.Nt * lattice.V3 != sites.numel():
+        raise ValueError("sites size is not a multiple of Nt*V3")
+    moms = [tuple(m) for m in moms]
+    if out is None:
+        out = torch.empty((n_chan, len(moms), lattice.Nt), dtype=torch.complex128, device=sites.device)
+    flat = [c for m in moms for c in m]
+    _check(_lib.qdpg_momentum_project(lattice._h, ctypes.c_void_p(sites.data_ptr()), n_chan, _ints(flat), len(moms),
+                                      _ints(origin) if origin is not None else None,
+                                      ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def momenta_up_to(n2max: int = 4):
+    """Integer momenta (nx, ny, nz) with nx^2 + ny^2 + nz^2 <= n2max (33 for 4)."""
+    r = int(n2max ** 0.5)
+    return [(a, b, c) for a in range(-r, r + 1) for b in range(-r, r + 1) for c in range(-r, r + 1)
+            if a * a + b * b + c * c <= n2max]
 
 
 SIXTEEN_MESONS = tuple((n, n) for n in range(16))

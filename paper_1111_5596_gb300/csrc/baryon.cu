@@ -198,9 +198,11 @@ __device__ __forceinline__ float2 baryon_term(const BaryonSpec& B, const float2*
   return make_float2(s * v.x, s * v.y);
 }
 
-template <typename PsiT, int KIND>
+// SITES: write the site value to sites[t][x] (complex FP32) instead of reducing.
+template <typename PsiT, int KIND, bool SITES>
 __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restrict__ Su, const PsiT* __restrict__ Sd,
-                                                             Geom g, BaryonSpec B, BMoms M, double* __restrict__ out) {
+                                                             Geom g, BaryonSpec B, BMoms M, double* __restrict__ out,
+                                                             float2* __restrict__ sites) {
   extern __shared__ float2 sm[];
   float2* su = sm;
   float2* sd = sm + kSites * kStride;
@@ -238,6 +240,10 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
       acc.x += __shfl_down_sync(0xffffffffu, acc.x, o);
       acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
     }
+    if constexpr (SITES) {
+      if (lane == 0) sites[(long long)t * V3 + s3] = acc;
+      continue;
+    }
     if (lane == 0) {
       int c0 = s3 % g.sL[0], c1 = (s3 / g.sL[0]) % g.sL[1], c2 = s3 / (g.sL[0] * g.sL[1]);
       for (int m = 0; m < M.n; ++m) {
@@ -258,6 +264,7 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
       }
     }
   }
+  if constexpr (SITES) return;
   __syncthreads();
   for (int m = threadIdx.x; m < M.n; m += blockDim.x) {
     double re = 0.0, im = 0.0;
@@ -277,9 +284,11 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
 
 using namespace qdpg;
 
-extern "C" int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const int* moms, int n_mom,
-                               const int origin[4], double* out_dev, void* stream) {
-  if (!Su || !moms || !out_dev) return fail(QDPG_ERR_ARG, "baryon_2pt: null argument");
+namespace {
+
+int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const int* moms, int n_mom,
+                  const int origin[4], double* out_dev, float2* sites, void* stream) {
+  if (!Su || !moms || (!out_dev && !sites)) return fail(QDPG_ERR_ARG, "baryon_2pt: null argument");
   if (kind != 0 && kind != 1) return fail(QDPG_ERR_ARG, "baryon_2pt: kind %d is neither 0 (nucleon) nor 1 (Delta)", kind);
   if (parity != 1 && parity != -1) return fail(QDPG_ERR_ARG, "baryon_2pt: parity must be +1 or -1");
   if (!Sd) {
@@ -329,17 +338,26 @@ extern "C" int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int p
     }
 
   cudaStream_t s = as_stream(stream);
-  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)n_mom * g.Nt, s);
-  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "baryon_2pt: memset: %s", cudaGetErrorString(e));
+  if (!sites) {
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)n_mom * g.Nt, s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "baryon_2pt: memset: %s", cudaGetErrorString(e));
+  }
   const size_t smem = sizeof(float2) * 2 * kSites * kStride + sizeof(double2) * kWarps * n_mom;
   dim3 grid((g.V3 + kSites - 1) / kSites, g.Nt);
   ProfScope prof("baryon_2pt", s);
 #define QDPG_BARYON_LAUNCH(T, KIND)                                                                          \
   do {                                                                                                       \
-    auto k = baryon_kernel<T, KIND>;                                                                         \
-    cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                        \
-    k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, M, \
-                                      out_dev);                                                              \
+    if (sites) {                                                                                             \
+      auto k = baryon_kernel<T, KIND, true>;                                                                 \
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+      k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, \
+                                        M, out_dev, sites);                                                  \
+    } else {                                                                                                 \
+      auto k = baryon_kernel<T, KIND, false>;                                                                \
+      cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+      k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, \
+                                        M, out_dev, sites);                                                  \
+    }                                                                                                        \
   } while (0)
   if (Su->prec == QDPG_BF16) {
     if (kind == 0) QDPG_BARYON_LAUNCH(__nv_bfloat162, 0);
@@ -350,4 +368,20 @@ extern "C" int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int p
   }
 #undef QDPG_BARYON_LAUNCH
   return check_launch("baryon_2pt");
+}
+
+}  // namespace
+
+extern "C" int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const int* moms, int n_mom,
+                               const int origin[4], double* out_dev, void* stream) {
+  if (!out_dev) return fail(QDPG_ERR_ARG, "baryon_2pt: null argument");
+  return baryon_common(Su, Sd, kind, parity, moms, n_mom, origin, out_dev, nullptr, stream);
+}
+
+extern "C" int qdpg_baryon_sites(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, void* sites_dev,
+                                 void* stream) {
+  if (!sites_dev) return fail(QDPG_ERR_ARG, "baryon_sites: null argument");
+  if (reinterpret_cast<uintptr_t>(sites_dev) % 8) return fail(QDPG_ERR_ARG, "baryon_sites: buffer not 8-byte aligned");
+  static const int zero[3] = {0, 0, 0};
+  return baryon_common(Su, Sd, kind, parity, zero, 1, nullptr, nullptr, static_cast<float2*>(sites_dev), stream);
 }

@@ -65,9 +65,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-template <int NQ, typename PsiT>
+// SITES: write each channel's site value c_j(x) to sites[row(j)][t][x]
+// (complex FP32) instead of reducing it.
+template <int NQ, typename PsiT, bool SITES>
 __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __restrict__ S1, const PsiT* __restrict__ S2,
-                                                              Geom g, MesonPass P, Moms M, double* __restrict__ out) {
+                                                              Geom g, MesonPass P, Moms M, double* __restrict__ out,
+                                                              float2* __restrict__ sites) {
   extern __shared__ double2 red[];  // [warp][nch * n_mom]
   const int s3 = blockIdx.x * kMesonThreads + threadIdx.x;
   const int t = blockIdx.y;
@@ -137,6 +140,10 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
         c.y = fmaf(w.x, Q[q][k].y, c.y);
         c.y = fmaf(w.y, Q[q][k].x, c.y);
       }
+      if constexpr (SITES) {
+        if (live) sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] = c;
+        continue;
+      }
       for (int m = 0; m < M.n; ++m) {
         float2 v = c;
         if (!M.zero_only) {
@@ -159,6 +166,7 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
       }
     }
   }
+  if constexpr (SITES) return;
   __syncthreads();
   const int nwarps = kMesonThreads / 32;
   for (int i = threadIdx.x; i < nv; i += kMesonThreads) {
@@ -180,25 +188,28 @@ struct Channel {
 };
 
 int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
-                cudaStream_t s) {
+                float2* sites, cudaStream_t s) {
   const Geom& g = S1->g;
   dim3 grid((g.V3 + kMesonThreads - 1) / kMesonThreads, g.Nt);
-  const size_t smem = (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
+  const size_t smem = sites ? 0 : (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
   const bool bf = S1->prec == QDPG_BF16;
   ProfScope prof("meson_2pt", s);
-#define QDPG_MESON_LAUNCH(NQ)                                                                                         \
-  do {                                                                                                                \
-    if (bf) {                                                                                                         \
-      auto k = meson_kernel<NQ, __nv_bfloat162>;                                                                      \
-      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-      k<<<grid, kMesonThreads, smem, s>>>(static_cast<const __nv_bfloat162*>(S1->data),                               \
-                                          static_cast<const __nv_bfloat162*>(S2->data), g, P, M, out);               \
-    } else {                                                                                                          \
-      auto k = meson_kernel<NQ, float2>;                                                                              \
-      if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);         \
-      k<<<grid, kMesonThreads, smem, s>>>(static_cast<const float2*>(S1->data), static_cast<const float2*>(S2->data), \
-                                          g, P, M, out);                                                              \
-    }                                                                                                                 \
+#define QDPG_MESON_KERNEL(NQ, T, SITES)                                                                 \
+  do {                                                                                                 \
+    auto k = meson_kernel<NQ, T, SITES>;                                                               \
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
+    k<<<grid, kMesonThreads, smem, s>>>(static_cast<const T*>(S1->data), static_cast<const T*>(S2->data), g, P, M, \
+                                        out, sites);                                                   \
+  } while (0)
+#define QDPG_MESON_LAUNCH(NQ)                                       \
+  do {                                                              \
+    if (bf) {                                                       \
+      if (sites) QDPG_MESON_KERNEL(NQ, __nv_bfloat162, true);       \
+      else QDPG_MESON_KERNEL(NQ, __nv_bfloat162, false);            \
+    } else {                                                        \
+      if (sites) QDPG_MESON_KERNEL(NQ, float2, true);               \
+      else QDPG_MESON_KERNEL(NQ, float2, false);                    \
+    }                                                               \
   } while (0)
   switch (P.nq) {
     case 1: QDPG_MESON_LAUNCH(1); break;
@@ -207,6 +218,7 @@ int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const q
     default: QDPG_MESON_LAUNCH(4); break;
   }
 #undef QDPG_MESON_LAUNCH
+#undef QDPG_MESON_KERNEL
   return check_launch("meson_2pt");
 }
 
@@ -216,11 +228,14 @@ int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const q
 
 using namespace qdpg;
 
-extern "C" {
+namespace qdpg {
+namespace {
 
-int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
-                   const int* moms, int n_mom, const int origin[4], double* out_dev, void* stream) {
-  if (!S1 || !S2 || !gamma_snk || !gamma_src || !moms || !out_dev) return fail(QDPG_ERR_ARG, "meson_2pt: null argument");
+// Shared by the reducing entry point (out_dev) and the site-value one (sites).
+int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
+                 const int* moms, int n_mom, const int origin[4], double* out_dev, float2* sites, void* stream) {
+  if (!S1 || !S2 || !gamma_snk || !gamma_src || !moms || (!out_dev && !sites))
+    return fail(QDPG_ERR_ARG, "meson_2pt: null argument");
   if (S1->kind != QDPG_PROPAGATOR || S2->kind != QDPG_PROPAGATOR)
     return fail(QDPG_ERR_SHAPE, "meson_2pt: S1 and S2 must be propagators");
   if ((S1->prec != QDPG_F32 && S1->prec != QDPG_BF16) || S2->prec != S1->prec)
@@ -265,13 +280,15 @@ int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const
       if (c.ma * 4 + c.mb == pair) sorted.push_back(c);
 
   cudaStream_t s = as_stream(stream);
-  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)n_chan * n_mom * g.Nt, s);
-  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "meson_2pt: memset: %s", cudaGetErrorString(e));
+  if (!sites) {
+    cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)n_chan * n_mom * g.Nt, s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "meson_2pt: memset: %s", cudaGetErrorString(e));
+  }
 
   MesonPass P{};
   auto flush = [&]() -> int {
     if (P.nch == 0) return QDPG_OK;
-    int rc = launch_pass(P, M, S1, S2, out_dev, s);
+    int rc = launch_pass(P, M, S1, S2, out_dev, sites, s);
     P = MesonPass{};
     return rc;
   };
@@ -295,6 +312,26 @@ int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const
     ++P.nch;
   }
   return flush();
+}
+
+}  // namespace
+}  // namespace qdpg
+
+extern "C" {
+
+int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
+                   const int* moms, int n_mom, const int origin[4], double* out_dev, void* stream) {
+  if (!out_dev) return fail(QDPG_ERR_ARG, "meson_2pt: null argument");
+  return meson_common(S1, S2, gamma_snk, gamma_src, n_chan, moms, n_mom, origin, out_dev, nullptr, stream);
+}
+
+int qdpg_meson_sites(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
+                     void* sites_dev, void* stream) {
+  if (!sites_dev) return fail(QDPG_ERR_ARG, "meson_sites: null argument");
+  if (reinterpret_cast<uintptr_t>(sites_dev) % 8) return fail(QDPG_ERR_ARG, "meson_sites: buffer not 8-byte aligned");
+  static const int zero[3] = {0, 0, 0};
+  return meson_common(S1, S2, gamma_snk, gamma_src, n_chan, zero, 1, nullptr, nullptr,
+                      static_cast<float2*>(sites_dev), stream);
 }
 
 }  // extern "C"
