@@ -142,27 +142,27 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
       }
       if constexpr (SITES) {
         if (live) sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] = c;
-        continue;
-      }
-      for (int m = 0; m < M.n; ++m) {
-        float2 v = c;
-        if (!M.zero_only) {
-          // phase index: sum_k n_k (x_k - o_k) V3/L_k  (mod V3), exact in integers
-          long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
-                          (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
-                          (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
-          num %= V3;
-          if (num < 0) num += V3;
-          float sn, cs;
-          sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
-          // v = c * (cs - i sn)
-          v = make_float2(c.x * cs + c.y * sn, c.y * cs - c.x * sn);
+      } else {
+        for (int m = 0; m < M.n; ++m) {
+          float2 v = c;
+          if (!M.zero_only) {
+            // phase index: sum_k n_k (x_k - o_k) V3/L_k  (mod V3), exact in integers
+            long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
+                            (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
+                            (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
+            num %= V3;
+            if (num < 0) num += V3;
+            float sn, cs;
+            sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
+            // v = c * (cs - i sn)
+            v = make_float2(c.x * cs + c.y * sn, c.y * cs - c.x * sn);
+          }
+          double re = live ? (double)v.x : 0.0;
+          double im = live ? (double)v.y : 0.0;
+          re = warp_sum(re);
+          im = warp_sum(im);
+          if (lane == 0) red[warp * nv + j * M.n + m] = make_double2(re, im);
         }
-        double re = live ? (double)v.x : 0.0;
-        double im = live ? (double)v.y : 0.0;
-        re = warp_sum(re);
-        im = warp_sum(im);
-        if (lane == 0) red[warp * nv + j * M.n + m] = make_double2(re, im);
       }
     }
   }
