@@ -130,7 +130,6 @@ int qdpg_device_status(void* stream);
  * and launch-shape settings of the pipelined smearing kernel:
  *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..256, 0 = default;
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
- *  QDPG_TUNE_SPLIT             consumer threads per site, 1 or 2, 0 = default;
  *  QDPG_TUNE_GRID              0: persistent CTAs (default), 1: one CTA per item. */
 enum {
   QDPG_DEBUG_WAIT_TIMEOUT_NS = 1,
@@ -138,7 +137,6 @@ enum {
   QDPG_DEBUG_FORCE_SIMPLE_HOP = 3,
   QDPG_TUNE_TILE_CONSUMERS = 4,
   QDPG_TUNE_STAGES = 5,
-  QDPG_TUNE_SPLIT = 6,
   QDPG_TUNE_GRID = 7
 };
 int qdpg_debug_set(int what, long long value);
@@ -300,6 +298,49 @@ int qdpg_baryon_sites(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, vo
  * n_chan*n_mom*Nt complex doubles, overwritten.  Limits: n_mom <= 64. */
 int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, int n_chan, const int* moms, int n_mom,
                           const int origin[4], double* out_dev, void* stream);
+
+/* ---- batches of independent jobs (Sec. 5: many sources at once) ---------- */
+
+/* One job of a batch: smear psi in place (n_iter iterations with kappa,
+ * exactly as qdpg_gauss_smear with scratch as the ping-pong buffer) and,
+ * if mesons_out is not NULL, then write the sixteen zero-momentum meson
+ * correlators of psi with itself (channel j = Gamma(j) at sink and source,
+ * as qdpg_meson_2pt with gamma_snk = gamma_src = 0..15, one momentum (0,0,0),
+ * origin 0) to mesons_out: a device buffer of 16*Nt complex doubles.
+ * The field headers are copied at qdpg_batch_create; the device buffers
+ * they point to are borrowed and must outlive the batch. */
+typedef struct {
+  qdpg_field_t U;       /* QDPG_GAUGE, any link precision */
+  qdpg_field_t psi;     /* PROPAGATOR or FERMION, F32 or BF16 (mesons: PROPAGATOR) */
+  qdpg_field_t scratch; /* same kind/precision/lattice as psi, distinct buffer */
+  double kappa;
+  int n_iter;           /* >= 0; jobs of one batch may differ */
+  double* mesons_out;   /* device, 16*Nt complex doubles, or NULL */
+} qdpg_job;
+
+typedef struct qdpg_batch* qdpg_batch_t; /* opaque, owned by the library */
+
+/* Plans a batch of njobs (1..4096) independent jobs; jobs may differ in
+ * lattice, precision, kappa and n_iter.  Jobs that share lattice, kind and
+ * precisions form one class; each smearing step runs one multi-job launch
+ * per class over the jobs whose count is not yet reached (up to 64 jobs per
+ * launch).  j_decay: the direction that is not smeared, as in
+ * qdpg_gauss_smear.  Errors: QDPG_ERR_ARG for a null pointer, njobs or
+ * j_decay out of range, negative n_iter or NaN kappa; QDPG_ERR_SHAPE for
+ * fields that do not match.  Nothing is launched or allocated on the device. */
+int qdpg_batch_create(const qdpg_job* jobs, int njobs, int j_decay, qdpg_batch_t* out);
+
+/* Runs every job of the batch on `stream`.  use_graph = 0: the launches are
+ * issued directly.  use_graph = 1: the first such call issues them directly
+ * (performing any one-time set-up) and then captures the same sequence into
+ * a CUDA graph (thread-local capture mode, on a stream the library creates
+ * and destroys for it, so `stream` may be the default stream) without running
+ * it again; later calls with use_graph = 1 launch that graph on `stream`.  Every run
+ * recomputes from the current contents of the jobs' psi buffers. */
+int qdpg_batch_run(qdpg_batch_t batch, int use_graph, void* stream);
+
+/* Frees the plan and its graph.  NULL is a no-op. */
+void qdpg_batch_destroy(qdpg_batch_t batch);
 
 #ifdef __cplusplus
 }

@@ -36,6 +36,13 @@ class QdpgError(RuntimeError):
         self.status = status
 
 
+class CJob(ctypes.Structure):
+    """Mirror of the C struct qdpg_job."""
+
+    _fields_ = [("U", ctypes.c_void_p), ("psi", ctypes.c_void_p), ("scratch", ctypes.c_void_p),
+                ("kappa", ctypes.c_double), ("n_iter", ctypes.c_int), ("mesons_out", ctypes.c_void_p)]
+
+
 def load() -> ctypes.CDLL:
     """Load libqdpg.so (built by ``__graft_entry__.build()``); raise if absent."""
     global _lib
@@ -75,6 +82,9 @@ def load() -> ctypes.CDLL:
         "qdpg_profile_enable": (i, [i]),
         "qdpg_profile_reset": (i, []),
         "qdpg_profile_query": (i, [ctypes.c_char_p, ctypes.POINTER(d), ctypes.POINTER(ctypes.c_uint64)]),
+        "qdpg_batch_create": (i, [ctypes.POINTER(CJob), i, i, vp]),
+        "qdpg_batch_run": (i, [vp, i, vp]),
+        "qdpg_batch_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -109,7 +119,7 @@ def launch_count() -> int:
 
 
 DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_STAGE, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
-TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_SPLIT, TUNE_GRID = 4, 5, 6, 7
+TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_GRID = 4, 5, 7
 
 
 def device_status(stream=None):
@@ -370,3 +380,41 @@ def momenta_up_to(n2max: int = 4):
 
 
 SIXTEEN_MESONS = tuple((n, n) for n in range(16))
+
+
+class Batch:
+    """Many independent smear (+ 16 zero-momentum mesons) jobs run together.
+
+    ``jobs``: sequence of ``(U, psi, scratch, kappa, n_iter, mesons)`` with
+    ``mesons`` a complex128 CUDA tensor of shape (16, Nt) or None.  Each run
+    smears every psi in place and, where ``mesons`` is given, writes
+    ``mesons[j, t]`` for channel Gamma(j) at sink and source."""
+
+    def __init__(self, jobs, j_decay: int = 3):
+        import torch
+
+        lib = load()
+        jobs = list(jobs)
+        arr = (CJob * max(1, len(jobs)))()
+        keep = []
+        for k, (U, psi, scratch, kappa, n_iter, mes) in enumerate(jobs):
+            if mes is not None:
+                if not (isinstance(mes, torch.Tensor) and mes.is_cuda and mes.dtype == torch.complex128
+                        and mes.is_contiguous() and tuple(mes.shape) == (16, psi.lattice.Nt)):
+                    raise ValueError("mesons must be a contiguous complex128 CUDA tensor of shape (16, Nt)")
+            arr[k] = CJob(U._h, psi._h, scratch._h, float(kappa), int(n_iter),
+                          mes.data_ptr() if mes is not None else None)
+            keep.append((U, psi, scratch, mes))
+        h = ctypes.c_void_p()
+        _check(lib.qdpg_batch_create(arr, len(jobs), int(j_decay), ctypes.byref(h)))
+        self._h, self._keep = h, keep
+
+    def run(self, use_graph: bool = False, stream=None):
+        """Issue every job on the stream; with ``use_graph`` the first call also
+        captures a CUDA graph that later calls launch."""
+        _check(_lib.qdpg_batch_run(self._h, 1 if use_graph else 0, _stream(stream)))
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _lib is not None:
+            _lib.qdpg_batch_destroy(self._h)
+            self._h = None

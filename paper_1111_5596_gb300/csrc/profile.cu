@@ -42,6 +42,10 @@ cudaEvent_t take_event() {
 ProfScope::ProfScope(const char* name, cudaStream_t s) : active_(false), idx_(0), s_(s) {
   std::lock_guard<std::mutex> lk(g_mu);
   if (!g_on || g_recs.size() >= 65536) return;
+  // Events recorded into a stream capture cannot be timed later: launches
+  // captured into a graph are not profiled.
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) return;
   Record r{name, take_event(), take_event()};
   if (!r.start || !r.stop) return;
   cudaEventRecord(r.start, s);

@@ -61,7 +61,6 @@ int debug_drop_vector();
 bool debug_force_simple_hop();
 int debug_tile_consumers();  // max consumer threads per pipelined tile, 0 = per-geometry default
 int debug_tile_stages();     // pipeline depth, 0 = as many as fit the shared-memory budget
-int debug_tile_split();      // consumer threads per site (1 or 2), 0 = default
 int debug_tile_grid();       // 0: persistent CTAs, 1: one CTA per work item
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage
@@ -71,6 +70,13 @@ constexpr unsigned int kStatusDrain = 4u;      // producer gave up draining its 
 // geometry or precision does not fit it, so the caller can use another kernel.
 int launch_hop_tma(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
                    const int hop_mu[3], float kappa, cudaStream_t s);
+// One hop with whichever smearing kernel serves the geometry.
+int launch_hop_any(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
+                   const int hop_mu[3], float kappa, cudaStream_t s);
+// One pipelined hop over several jobs on the same lattice and precisions
+// (each job its own in/out/links/kappa); QDPG_ERR_UNSUPPORTED as above.
+int launch_hop_tma_batch(const void* const* in, void* const* out, const void* const* U, const float* kappa, int njobs,
+                         int lprec, int psi_prec, const Geom& g, const int hop_mu[3], cudaStream_t s);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

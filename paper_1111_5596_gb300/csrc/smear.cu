@@ -134,6 +134,15 @@ bool same_lattice(const Geom& a, const Geom& b) {
 
 }  // namespace
 
+// One hop psi -> out with whichever kernel serves the geometry (see launch_hop).
+int launch_hop_any(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
+                   const int hop_mu[3], float kappa, cudaStream_t s) {
+  HopDirs hd;
+  for (int i = 0; i < 3; ++i) hd.mu[i] = hop_mu[i];
+  if (psi_prec == QDPG_BF16) return launch_hop<__nv_bfloat162>(in, out, U, lprec, g, hd, kappa, cols, s);
+  return launch_hop<float2>(in, out, U, lprec, g, hd, kappa, cols, s);
+}
+
 }  // namespace qdpg
 
 using namespace qdpg;

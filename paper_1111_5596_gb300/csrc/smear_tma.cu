@@ -29,8 +29,8 @@ int sm_count() {
 
 // Tile of k plane rows: the largest divisor k of Ly with Lx*k <= max_consumers;
 // pipeline depth from what shared memory leaves after the link buffer.
-bool pick_tile(const Geom& g, int esize, int link_esize, int link_ne, int max_consumers, int stages, int split,
-               int grid_mode, TmaTile& tt) {
+bool pick_tile(const Geom& g, int esize, int link_esize, int link_ne, int max_consumers, int stages, int grid_mode,
+               int njobs, TmaTile& tt) {
   const int Lx = g.sL[0], Ly = g.sL[1];
   if ((Lx * esize) % 16 != 0 || (Lx * link_esize) % 16 != 0) return false;
   int best = 0;
@@ -39,8 +39,7 @@ bool pick_tile(const Geom& g, int esize, int link_esize, int link_ne, int max_co
   if (best == 0) return false;
   tt.k = best;
   tt.ntiles_y = Ly / best;
-  tt.split = split;
-  tt.cwarps = (split * Lx * best + 31) / 32;
+  tt.cwarps = (Lx * best + 31) / 32;
   tt.halo = best == Ly ? 0 : 1;
   tt.rowsA = best + 2 * tt.halo;
   tt.rows = tt.rowsA + 2 * best;
@@ -61,7 +60,8 @@ bool pick_tile(const Geom& g, int esize, int link_esize, int link_ne, int max_co
   const int nsm = sm_count();
   if (nsm <= 0) return false;
   // persistent: one resident wave of CTAs walks the items; otherwise one CTA per item
-  tt.grid = (grid_mode == 1 || tt.nitems < nsm * per_sm) ? tt.nitems : nsm * per_sm;
+  const int total = tt.nitems * njobs;
+  tt.grid = (grid_mode == 1 || total < nsm * per_sm) ? total : nsm * per_sm;
   return true;
 }
 
@@ -75,7 +75,6 @@ int default_consumers(const Geom& g) { return g.sL[0] >= 24 ? 128 : 256; }
 struct TileCfg {
   int consumers;  // most sites per tile
   int grid_mode;  // 0 persistent, 1 one CTA per item
-  int split;      // consumer threads per site
   int stages;     // 0: as many as fit
 };
 
@@ -102,8 +101,8 @@ TuneKey key_of(const Geom& g, int psi_prec, int lprec) {
 // The configuration a launch uses: explicit tuning settings first, then the
 // autotuning table, then the defaults.
 TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
-  TileCfg c{debug_tile_consumers(), debug_tile_grid(), debug_tile_split(), debug_tile_stages()};
-  const bool explicit_cfg = c.consumers || c.grid_mode || c.split || c.stages;
+  TileCfg c{debug_tile_consumers(), debug_tile_grid(), debug_tile_stages()};
+  const bool explicit_cfg = c.consumers || c.grid_mode || c.stages;
   if (!explicit_cfg) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key_of(g, psi_prec, lprec));
@@ -113,28 +112,30 @@ TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
   return c;
 }
 
-int launch_hop_tma_cfg(const void* in, void* out, const void* U, int lprec, int psi_prec, const Geom& g, float kappa,
+int launch_hop_tma_cfg(const tma_smear::JobPtrs* jobs, int njobs, int lprec, int psi_prec, const Geom& g,
                        cudaStream_t s, const TileCfg& cfg) {
+  if (njobs < 1 || njobs > tma_smear::kMaxJobs) return QDPG_ERR_UNSUPPORTED;
   const bool bf = psi_prec == QDPG_BF16;
   tma_smear::HopLaunch a;
   const bool lr12 = lprec == QDPG_F32_R12 || lprec == QDPG_BF16_R12;
   const int lesize = (lprec == QDPG_F32 || lprec == QDPG_F32_R12) ? 8 : 4;
-  // the lane-pair split is instantiated for matching storage/link precisions only
-  const bool matched = bf ? (lprec == QDPG_BF16 || lprec == QDPG_BF16_R12) : (lprec == QDPG_F32 || lprec == QDPG_F32_R12);
-  const int split = matched && cfg.split == 2 ? 2 : 1;
-  if (!pick_tile(g, bf ? 4 : 8, lesize, lr12 ? 6 : 9, cfg.consumers, cfg.stages, split, cfg.grid_mode, a.tt))
+  if (!pick_tile(g, bf ? 4 : 8, lesize, lr12 ? 6 : 9, cfg.consumers, cfg.stages, cfg.grid_mode, njobs, a.tt))
     return QDPG_ERR_UNSUPPORTED;
   a.status = device_status_word();
   if (!a.status) return QDPG_ERR_UNSUPPORTED;
-  a.in = in;
-  a.out = out;
-  a.U = U;
+  a.jobs.njobs = njobs;
+  for (int i = 0; i < njobs; ++i) a.jobs.j[i] = jobs[i];
   a.g = g;
-  a.kappa = kappa;
   a.timeout_ns = wait_timeout_ns();
   a.drop_stage = debug_drop_vector();
   a.stream = s;
   return bf ? tma_smear::launch_tma_bf16(lprec, a) : tma_smear::launch_tma_f32(lprec, a);
+}
+
+int launch_one(const void* in, void* out, const void* U, int lprec, int psi_prec, const Geom& g, float kappa,
+               cudaStream_t s, const TileCfg& cfg) {
+  tma_smear::JobPtrs j{in, out, U, kappa};
+  return launch_hop_tma_cfg(&j, 1, lprec, psi_prec, g, s, cfg);
 }
 
 bool tma_eligible(int cols, const Geom& g, const int hop_mu[3]) {
@@ -149,7 +150,16 @@ bool tma_eligible(int cols, const Geom& g, const int hop_mu[3]) {
 int launch_hop_tma(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
                    const int hop_mu[3], float kappa, cudaStream_t s) {
   if (!tma_eligible(cols, g, hop_mu)) return QDPG_ERR_UNSUPPORTED;
-  return launch_hop_tma_cfg(in, out, U, lprec, psi_prec, g, kappa, s, current_cfg(g, psi_prec, lprec));
+  return launch_one(in, out, U, lprec, psi_prec, g, kappa, s, current_cfg(g, psi_prec, lprec));
+}
+
+int launch_hop_tma_batch(const void* const* in, void* const* out, const void* const* U, const float* kappa, int njobs,
+                         int lprec, int psi_prec, const Geom& g, const int hop_mu[3], cudaStream_t s) {
+  if (!tma_eligible(12, g, hop_mu)) return QDPG_ERR_UNSUPPORTED;
+  tma_smear::JobPtrs jobs[tma_smear::kMaxJobs];
+  if (njobs > tma_smear::kMaxJobs) return QDPG_ERR_UNSUPPORTED;
+  for (int i = 0; i < njobs; ++i) jobs[i] = tma_smear::JobPtrs{in[i], out[i], U[i], kappa[i]};
+  return launch_hop_tma_cfg(jobs, njobs, lprec, psi_prec, g, s, current_cfg(g, psi_prec, lprec));
 }
 
 }  // namespace qdpg
@@ -175,7 +185,7 @@ int qdpg_tune_smear(qdpg_field_t U, qdpg_field_t psi, qdpg_field_t scratch, int 
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(QDPG_ERR_CUDA, "tune_smear: event creation failed");
   static const int consumer_opts[] = {256, 192, 128, 96, 64, 48, 32};
-  TileCfg best{0, 0, 1, 0};
+  TileCfg best{0, 0, 0};
   float best_us = 0.f;
   int last_k = -1;
   int rc = QDPG_OK;
@@ -187,13 +197,13 @@ int qdpg_tune_smear(qdpg_field_t U, qdpg_field_t psi, qdpg_field_t scratch, int 
     if (kk == 0 || kk == last_k) continue;
     last_k = kk;
     for (int gm = 0; gm < 2 && rc == QDPG_OK; ++gm) {
-      const TileCfg cfg{consumer_opts[ci], gm, 1, 0};
-      int r = launch_hop_tma_cfg(psi->data, scratch->data, U->data, U->prec, psi->prec, g, 0.1f, s, cfg);
+      const TileCfg cfg{consumer_opts[ci], gm, 0};
+      int r = launch_one(psi->data, scratch->data, U->data, U->prec, psi->prec, g, 0.1f, s, cfg);
       if (r == QDPG_ERR_UNSUPPORTED) continue;
       if (r != QDPG_OK) { rc = r; break; }
       cudaEventRecord(e0, s);
       for (int i = 0; i < reps && r == QDPG_OK; ++i)
-        r = launch_hop_tma_cfg(psi->data, scratch->data, U->data, U->prec, psi->prec, g, 0.1f, s, cfg);
+        r = launch_one(psi->data, scratch->data, U->data, U->prec, psi->prec, g, 0.1f, s, cfg);
       cudaEventRecord(e1, s);
       if (r != QDPG_OK) { rc = r; break; }
       if (cudaEventSynchronize(e1) != cudaSuccess) { rc = fail(QDPG_ERR_CUDA, "tune_smear: timing failed"); break; }
@@ -231,12 +241,12 @@ int qdpg_tune_save(const char* path) {
   std::lock_guard<std::mutex> lk(g_tune_mu);
   FILE* f = fopen(path, "w");
   if (!f) return fail(QDPG_ERR_ARG, "tune_save: cannot open %s", path);
-  fprintf(f, "# L0 L1 L2 L3 j_decay psi_prec link_prec consumers grid_mode split stages us_per_hop\n");
+  fprintf(f, "# L0 L1 L2 L3 j_decay psi_prec link_prec consumers grid_mode stages us_per_hop\n");
   for (const auto& kv : g_tune) {
     const TuneKey& k = kv.first;
     const TileCfg& c = kv.second.first;
-    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d %.3f\n", k.L[0], k.L[1], k.L[2], k.L[3], k.jd, k.psi, k.link,
-            c.consumers, c.grid_mode, c.split, c.stages, kv.second.second);
+    fprintf(f, "%d %d %d %d %d %d %d %d %d %d %.3f\n", k.L[0], k.L[1], k.L[2], k.L[3], k.jd, k.psi, k.link,
+            c.consumers, c.grid_mode, c.stages, kv.second.second);
   }
   fclose(f);
   return ok();
@@ -254,11 +264,10 @@ int qdpg_tune_load(const char* path) {
     TuneKey k;
     TileCfg c;
     float us = 0.f;
-    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d %f", &k.L[0], &k.L[1], &k.L[2], &k.L[3], &k.jd, &k.psi,
-               &k.link, &c.consumers, &c.grid_mode, &c.split, &c.stages, &us) != 12)
+    if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %f", &k.L[0], &k.L[1], &k.L[2], &k.L[3], &k.jd, &k.psi,
+               &k.link, &c.consumers, &c.grid_mode, &c.stages, &us) != 11)
       continue;
-    if (c.consumers < 32 || c.consumers > 256 || c.grid_mode < 0 || c.grid_mode > 1 || c.split < 1 || c.split > 2 ||
-        c.stages < 0 || c.stages > 16)
+    if (c.consumers < 32 || c.consumers > 256 || c.grid_mode < 0 || c.grid_mode > 1 || c.stages < 0 || c.stages > 16)
       continue;
     g_tune[k] = {c, us};
     ++n;

@@ -62,16 +62,26 @@ struct TmaTile {
   int nitems;     // tiles * kSplit
   int grid;       // persistent CTAs
   int smem;       // dynamic shared memory bytes
-  int split;      // consumer threads per site: 1 or 2
 };
 
-struct HopLaunch {
+// Jobs of one launch: same lattice and precisions, own fields and kappa.
+// Work items are job-major: item i belongs to job i / TmaTile::nitems.
+constexpr int kMaxJobs = 64;
+struct JobPtrs {
   const void* in;
   void* out;
   const void* U;
+  float kappa;
+};
+struct JobTable {
+  int njobs;
+  JobPtrs j[kMaxJobs];
+};
+
+struct HopLaunch {
+  JobTable jobs;
   Geom g;
   TmaTile tt;
-  float kappa;
   unsigned int* status;
   long long timeout_ns;
   int drop_stage;
@@ -115,12 +125,9 @@ __device__ __forceinline__ void link_from_smem(const LT* p, int stride, float2 m
 // Threads per CTA (consumer warps + the producer warp) and the CTAs per SM
 // the register budget is sized for: tiles of at most 128 sites run two CTAs
 // per SM.
-// SPLIT = 1: one consumer thread per site; SPLIT = 2: a lane pair per site
-// (lane l the forward hops, lane l^16 the backward ones), half the link
-// registers per thread and twice the warps.
-template <int LX, int KR, int SPLIT>
+template <int LX, int KR>
 struct TileLaunch {
-  static constexpr int threads = LX ? ((SPLIT * LX * KR + 31) / 32 + 1) * 32 : SPLIT * kMaxConsumers + 32;
+  static constexpr int threads = LX ? ((LX * KR + 31) / 32 + 1) * 32 : kMaxConsumers + 32;
   static constexpr int min_blocks = (LX && LX * KR <= 96) ? 3 : ((LX && LX * KR <= 128) ? 2 : 1);
 };
 
@@ -142,10 +149,10 @@ __device__ __forceinline__ ItemPos decode_item(int it, const TmaTile& tt, int Lz
   return p;
 }
 
-template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G, int SPLIT>
-__global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch<LX, KR, SPLIT>::min_blocks)
-    smear_hop_tma_kernel(const PsiT* __restrict__ in, PsiT* __restrict__ out, const void* __restrict__ U, Geom g,
-                         TmaTile tt, float kappa, unsigned int* status, long long timeout_ns, int drop_stage) {
+template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G>
+__global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR>::min_blocks)
+    smear_hop_tma_kernel(const __grid_constant__ JobTable J, Geom g, TmaTile tt, unsigned int* status,
+                         long long timeout_ns, int drop_stage) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   typedef typename LinkTraits<LMODE>::T LT;
   constexpr int NE = LinkTraits<LMODE>::NE;
@@ -197,8 +204,10 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
     const int nlcopies = 4 * NE + (halo ? NE : 0);
     int gstage = 0, nitem = 0, last_link = -1;
     bool failed = false;
-    for (int it = blockIdx.x; it < tt.nitems && !failed; it += gridDim.x, ++nitem) {
-      const ItemPos p = decode_item(it, tt, Lz);
+    const int total = tt.nitems * J.njobs;
+    for (int it = blockIdx.x; it < total && !failed; it += gridDim.x, ++nitem) {
+      const int job = it / tt.nitems;
+      const ItemPos p = decode_item(it - job * tt.nitems, tt, Lz);
       const int zm = (p.z - 1 + Lz) % Lz, zp = (p.z + 1) % Lz;
       const int ym = (p.y0 - 1 + Ly) % Ly, yp = (p.y0 + k) % Ly;
       // links of the tile, once the consumers hold the previous item's in registers
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
       }
       if (lane == 0) ptx::mbar_arrive_expect_tx(lfull, link_bytes);
       __syncwarp();
-      const LT* Ut = static_cast<const LT*>(U) + (size_t)p.t * NCL * V3;
+      const LT* Ut = static_cast<const LT*>(J.j[job].U) + (size_t)p.t * NCL * V3;
       for (int cp = lane; cp < nlcopies; cp += 32) {
         int comp, src_off, dst, n;
         if (cp < 3 * NE) {  // F[i][e]
@@ -238,7 +247,7 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
       }
       last_link = nitem;
       // the item's colour vectors, G per stage
-      const PsiT* base_t = in + (size_t)p.t * NC * V3;
+      const PsiT* base_t = static_cast<const PsiT*>(J.j[job].in) + (size_t)p.t * NC * V3;
       for (int j = 0; j < SPI; ++j, ++gstage) {
         const int s = gstage % S, n = gstage / S;
         if (n > 0) {
@@ -291,14 +300,10 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
   }
 
   // ---------------- consumer warps ----------------
-  // SPLIT == 1: thread ctid owns site ctid.  SPLIT == 2: warp w covers sites
-  // 16w..16w+15; lanes 0-15 apply the forward hops, lanes 16-31 the backward
-  // hops of the same sites, and the forward lane adds both halves.
-  const int sidx = SPLIT == 1 ? threadIdx.x : (warp * 16 + (lane & 15));
-  const int role = SPLIT == 1 ? 0 : (lane >> 4);  // 0: forward (and the only role when SPLIT == 1)
-  const bool active = sidx < kLx;
-  const int r = active ? sidx / Lx : 0;
-  const int x = active ? sidx % Lx : 0;
+  const int ctid = threadIdx.x;
+  const bool active = ctid < kLx;
+  const int r = active ? ctid / Lx : 0;
+  const int x = active ? ctid % Lx : 0;
   const int xm = x == 0 ? Lx - 1 : x - 1;
   // shared-memory offsets (elements, within a colour region) of the seven sites
   const int rc = r + halo;
@@ -307,9 +312,6 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
   const int ym_row = halo ? r : (r == 0 ? k - 1 : r - 1);
   const int of[3] = {rc * Lx + (x + 1 == Lx ? 0 : x + 1), yp_row * Lx + x, (rowsA + k + r) * Lx + x};
   const int ob[3] = {rc * Lx + xm, ym_row * Lx + x, (rowsA + r) * Lx + x};
-  int on[3];  // this lane's neighbours
-#pragma unroll
-  for (int i = 0; i < 3; ++i) on[i] = role ? ob[i] : of[i];
   // link-buffer offsets of this site's six links
   const int lf = r * Lx + x;
   const bool yh = halo && r == 0;
@@ -317,45 +319,31 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
   const int lyb_stride = yh ? Lx : kLx;
 
   int gstage = 0, nitem = 0;
-  for (int it = blockIdx.x; it < tt.nitems; it += gridDim.x, ++nitem) {
-    const ItemPos p = decode_item(it, tt, Lz);
+  const int total = tt.nitems * J.njobs;
+  for (int it = blockIdx.x; it < total; it += gridDim.x, ++nitem) {
+    const int job = it / tt.nitems;
+    const ItemPos p = decode_item(it - job * tt.nitems, tt, Lz);
+    const float kappa = J.j[job].kappa;
     bool ok = ptx::mbar_wait_bounded(lfull, nitem & 1, timeout_ns);
     if (!__all_sync(0xffffffffu, ok)) {
       if (lane == 0) atomicOr(status, kStatusFullWait);
       return;
     }
     SiteLinks L;
-    u64 M[3][9];  // SPLIT == 2: this lane's half of the links
     if (active) {
-      if constexpr (SPLIT == 1) {
-        float2 Uf[3][9], Ub[3][9];
+      float2 Uf[3][9], Ub[3][9];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) link_from_smem<LMODE>(lbuf + i * NE * kLx + lf, kLx, Uf[i]);
-        link_from_smem<LMODE>(lbuf + r * Lx + xm, kLx, Ub[0]);
-        link_from_smem<LMODE>(lbuf + lyb, lyb_stride, Ub[1]);
-        link_from_smem<LMODE>(lbuf + lk_ZB + lf, kLx, Ub[2]);
-        make_site_links(Uf, Ub, L);
-      } else {
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-          const LT* lp = role == 0 ? lbuf + i * NE * kLx + lf
-                                   : (i == 0 ? lbuf + r * Lx + xm : (i == 1 ? lbuf + lyb : lbuf + lk_ZB + lf));
-          const int lstr = (role == 1 && i == 1) ? lyb_stride : kLx;
-          float2 m[9];
-          link_from_smem<LMODE>(lp, lstr, m);
-#pragma unroll
-          for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int q = 0; q < 3; ++q)
-              M[i][a * 3 + q] = role == 0 ? pack2(m[a * 3 + q]) : pack2(m[q * 3 + a].x, -m[q * 3 + a].y);
-        }
-      }
+      for (int i = 0; i < 3; ++i) link_from_smem<LMODE>(lbuf + i * NE * kLx + lf, kLx, Uf[i]);
+      link_from_smem<LMODE>(lbuf + r * Lx + xm, kLx, Ub[0]);
+      link_from_smem<LMODE>(lbuf + lyb, lyb_stride, Ub[1]);
+      link_from_smem<LMODE>(lbuf + lk_ZB + lf, kLx, Ub[2]);
+      make_site_links(Uf, Ub, L);
     }
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(lempty);
 
     const int s3 = x + Lx * ((p.y0 + r) + Ly * p.z);
-    PsiT* outp = out + (size_t)p.t * NC * V3 + s3;
+    PsiT* outp = static_cast<PsiT*>(J.j[job].out) + (size_t)p.t * NC * V3 + s3;
     for (int j = 0; j < SPI; ++j, ++gstage) {
       const int s = gstage % S, n = gstage / S;
       ok = ptx::mbar_wait_bounded(full0 + 8 * s, n & 1, timeout_ns);
@@ -363,52 +351,27 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR, SPLIT>::threads, TileLaunch
         if (lane == 0) atomicOr(status, kStatusFullWait);
         return;
       }
-      const PsiT* sp = st + (size_t)s * stage_elems;
-      const int v0 = p.part * VPI + j * G;
-      PsiT* po = outp + (size_t)((v0 / COLS) * 3 * COLS + (v0 % COLS)) * V3;
+      if (active) {
+        const PsiT* sp = st + (size_t)s * stage_elems;
+        const int v0 = p.part * VPI + j * G;
+        PsiT* po = outp + (size_t)((v0 / COLS) * 3 * COLS + (v0 % COLS)) * V3;
 #pragma unroll
-      for (int gg = 0; gg < G; ++gg) {
-        const PsiT* sg = sp + gg * 3 * CS;
-        if constexpr (SPLIT == 1) {
-          if (active) {
-            u64 nf[3][3], nb[3][3];
-            float2 c[3], o[3];
+        for (int gg = 0; gg < G; ++gg) {
+          const PsiT* sg = sp + gg * 3 * CS;
+          u64 nf[3][3], nb[3][3];
+          float2 c[3], o[3];
 #pragma unroll
-            for (int i = 0; i < 3; ++i)
+          for (int i = 0; i < 3; ++i)
 #pragma unroll
-              for (int q = 0; q < 3; ++q) {
-                nf[i][q] = lds_pair(sg + of[i] + q * CS);
-                nb[i][q] = lds_pair(sg + ob[i] + q * CS);
-              }
-#pragma unroll
-            for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * CS);
-            hop_vector(L, nf, nb, c, kappa, o);
-#pragma unroll
-            for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);
-          }
-        } else {
-          float2 h[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-          if (active) {
-            u64 nn[3][3];
-#pragma unroll
-            for (int i = 0; i < 3; ++i)
-#pragma unroll
-              for (int q = 0; q < 3; ++q) nn[i][q] = lds_pair(sg + on[i] + q * CS);
-            hop_half(M, nn, h);
-          }
-          float2 hb[3];
-#pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            hb[a].x = __shfl_xor_sync(0xffffffffu, h[a].x, 16);
-            hb[a].y = __shfl_xor_sync(0xffffffffu, h[a].y, 16);
-          }
-          if (active && role == 0) {
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              const float2 c = lds(sg + oc + a * CS);
-              st2(po + (gg + a * COLS) * V3, hop_combine(c, h[a], hb[a], kappa));
+            for (int q = 0; q < 3; ++q) {
+              nf[i][q] = lds_pair(sg + of[i] + q * CS);
+              nb[i][q] = lds_pair(sg + ob[i] + q * CS);
             }
-          }
+#pragma unroll
+          for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * CS);
+          hop_vector(L, nf, nb, c, kappa, o);
+#pragma unroll
+          for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);
         }
       }
       __syncwarp();
@@ -425,15 +388,14 @@ inline size_t tma_smem_bytes(const TmaTile& tt, int Lx, int NE) {
   return tt.stages * stage_bytes + lbytes + (2 * tt.stages + 2) * sizeof(uint64_t);
 }
 
-template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G, int SPLIT>
+template <typename PsiT, int LMODE, int LX, int KR, int HALO, int G>
 int launch_tma_t(const HopLaunch& a) {
-  auto kern = smear_hop_tma_kernel<PsiT, LMODE, LX, KR, HALO, G, SPLIT>;
+  auto kern = smear_hop_tma_kernel<PsiT, LMODE, LX, KR, HALO, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.tt.smem);
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "gauss_smear: smem attribute: %s", cudaGetErrorString(e));
   dim3 block(32 * (a.tt.cwarps + 1));
   ProfScope prof("smear_hop", a.stream);
-  kern<<<a.tt.grid, block, a.tt.smem, a.stream>>>(static_cast<const PsiT*>(a.in), static_cast<PsiT*>(a.out), a.U,
-                                                  a.g, a.tt, a.kappa, a.status, a.timeout_ns, a.drop_stage);
+  kern<<<a.tt.grid, block, a.tt.smem, a.stream>>>(a.jobs, a.g, a.tt, a.status, a.timeout_ns, a.drop_stage);
   return check_launch("gauss_smear hop (pipelined)");
 }
 
@@ -454,13 +416,11 @@ template <typename PsiT, int LMODE>
 int launch_tma_any(const HopLaunch& a) {
   const int Lx = a.g.sL[0];
   constexpr int G = 2;
-#define QDPG_TMA_TRY(LXV, KV, HV)                                              \
-  if (Lx == LXV && a.tt.k == KV && a.tt.halo == HV)                            \
-    return a.tt.split == 2 ? launch_tma_t<PsiT, LMODE, LXV, KV, HV, G, 2>(a)   \
-                           : launch_tma_t<PsiT, LMODE, LXV, KV, HV, G, 1>(a);
+#define QDPG_TMA_TRY(LXV, KV, HV) \
+  if (Lx == LXV && a.tt.k == KV && a.tt.halo == HV) return launch_tma_t<PsiT, LMODE, LXV, KV, HV, G>(a);
   QDPG_TMA_FIXED_SHAPES(QDPG_TMA_TRY)
 #undef QDPG_TMA_TRY
-  return a.tt.split == 2 ? launch_tma_t<PsiT, LMODE, 0, 0, 0, G, 2>(a) : launch_tma_t<PsiT, LMODE, 0, 0, 0, G, 1>(a);
+  return launch_tma_t<PsiT, LMODE, 0, 0, 0, G>(a);
 }
 
 int launch_tma_f32(int lprec, const HopLaunch& a);

@@ -8,8 +8,8 @@ int launch_tma_f32(int lprec, const HopLaunch& a) {
   switch (lprec) {
     case QDPG_F32: return launch_tma_any<float2, L_F32>(a);
     case QDPG_F32_R12: return launch_tma_any<float2, L_F32_R12>(a);
-    case QDPG_BF16: return launch_tma_t<float2, L_BF16, 0, 0, 0, 2, 1>(a);
-    case QDPG_BF16_R12: return launch_tma_t<float2, L_BF16_R12, 0, 0, 0, 2, 1>(a);
+    case QDPG_BF16: return launch_tma_t<float2, L_BF16, 0, 0, 0, 2>(a);
+    case QDPG_BF16_R12: return launch_tma_t<float2, L_BF16_R12, 0, 0, 0, 2>(a);
   }
   return QDPG_ERR_UNSUPPORTED;
 }

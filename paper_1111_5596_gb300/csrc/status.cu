@@ -18,7 +18,6 @@ int g_drop_vector = -1;
 bool g_force_simple = false;
 int g_tile_consumers = 0;  // 0: the library's default for the geometry
 int g_tile_stages = 0;
-int g_tile_split = 0;
 int g_tile_grid = 0;
 
 }  // namespace
@@ -40,7 +39,6 @@ int debug_drop_vector() { return g_drop_vector; }
 bool debug_force_simple_hop() { return g_force_simple; }
 int debug_tile_consumers() { return g_tile_consumers; }
 int debug_tile_stages() { return g_tile_stages; }
-int debug_tile_split() { return g_tile_split; }
 int debug_tile_grid() { return g_tile_grid; }
 
 }  // namespace qdpg
@@ -88,10 +86,6 @@ int qdpg_debug_set(int what, long long value) {
     case QDPG_TUNE_STAGES:
       if (value != 0 && (value < 2 || value > 16)) return fail(QDPG_ERR_ARG, "debug_set: stages outside 2..16");
       g_tile_stages = (int)value;
-      return ok();
-    case QDPG_TUNE_SPLIT:
-      if (value < 0 || value > 2) return fail(QDPG_ERR_ARG, "debug_set: split outside 0..2");
-      g_tile_split = (int)value;
       return ok();
     case QDPG_TUNE_GRID:
       if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: grid mode outside 0..1");

@@ -155,3 +155,45 @@ def test_operation_argument_errors_are_caught_on_host(q):
     assert L.qdpg_field_import(P, None, 0, None) == ERR_ARG
     assert L.qdpg_field_import(P, out, 7, None) == ERR_DTYPE
     assert q.launch_count() == launches_before                    # every error came before a launch
+
+
+@host_only
+def test_batch_planning_validates_jobs_on_host(q):
+    L = q._lib
+    launches_before = q.launch_count()
+    _, lat = _lat(q, (4, 4, 4, 4))
+    _, lat2 = _lat(q, (4, 4, 4, 6))
+    U = _wrap(q, lat, q.GAUGE, q.F32, 1 << 24)
+    P = _wrap(q, lat, q.PROPAGATOR, q.F32, 1 << 26)
+    Ps = _wrap(q, lat, q.PROPAGATOR, q.F32, 1 << 27)
+    P2 = _wrap(q, lat2, q.PROPAGATOR, q.F32, 1 << 28)
+    F = _wrap(q, lat, q.FERMION, q.F32, 1 << 30)
+    Fb = _wrap(q, lat, q.FERMION, q.BF16, 1 << 31)
+    mes = 1 << 34
+
+    def create(*jobs, jd=3):
+        arr = (q.CJob * max(1, len(jobs)))(*[q.CJob(*j) for j in jobs])
+        h = ctypes.c_void_p()
+        rc = L.qdpg_batch_create(arr, len(jobs), jd, ctypes.byref(h))
+        if rc == OK:
+            L.qdpg_batch_destroy(h)
+        return rc
+
+    good = (U, P, Ps, 0.2, 3, mes)
+    assert create(good) == OK
+    assert create(good, (U, F, _wrap(q, lat, q.FERMION, q.F32, 1 << 29), 0.1, 0, None)) == OK
+    assert create(jd=4, *[good]) == ERR_ARG
+    assert create() == ERR_ARG                                   # no jobs
+    assert create((None, P, Ps, 0.2, 3, None)) == ERR_ARG
+    assert create((P, P, Ps, 0.2, 3, None)) == ERR_SHAPE         # U must be a gauge field
+    assert create((U, P, P, 0.2, 3, None)) == ERR_SHAPE          # scratch aliases psi
+    assert create((U, P, F, 0.2, 3, None)) == ERR_SHAPE          # scratch kind
+    assert create((U, F, Fb, 0.2, 3, None)) == ERR_SHAPE         # scratch precision
+    assert create((U, P2, Ps, 0.2, 3, None)) == ERR_SHAPE        # different lattice
+    assert create((U, P, Ps, float("nan"), 3, None)) == ERR_ARG
+    assert create((U, P, Ps, 0.2, -1, None)) == ERR_ARG
+    assert create((U, F, Fb, 0.2, 3, mes)) == ERR_SHAPE          # mesons need a propagator
+    assert L.qdpg_batch_create(None, 1, 3, ctypes.byref(ctypes.c_void_p())) == ERR_ARG
+    assert L.qdpg_batch_run(None, 0, None) == ERR_ARG
+    L.qdpg_batch_destroy(None)
+    assert q.launch_count() == launches_before
