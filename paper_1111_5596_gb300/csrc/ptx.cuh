@@ -23,6 +23,13 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 }
 
 // Make mbarrier initialisation visible to the async proxy (bulk copies).
+// Programmatic dependent launch: let the next kernel in the stream start its
+// CTAs (which then run up to their dependency wait) / wait until every
+// kernel this one depends on has completed and its writes are visible.
+// Both are no-ops for a kernel launched without the programmatic attribute.
+__device__ __forceinline__ void launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void wait_dependencies() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 __device__ __forceinline__ void fence_mbar_init() {
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }

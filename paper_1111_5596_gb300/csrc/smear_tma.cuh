@@ -196,6 +196,9 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
     ptx::fence_mbar_init();
   }
   __syncthreads();
+  // The next hop may begin its own set-up while this one runs; its reads and
+  // writes of the spinor buffers wait for this grid to complete.
+  ptx::launch_dependents();
 
   if (warp == tt.cwarps) {
     // ---------------- producer warp ----------------
@@ -203,6 +206,7 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
     const int ncopies = G * 3 * npieces;
     const int nlcopies = 4 * NE + (halo ? NE : 0);
     int gstage = 0, nitem = 0, last_link = -1;
+    int s = 0, n = 0;  // slot and round of stage gstage (gstage = n*S + s), kept without division
     bool failed = false;
     const int total = tt.nitems * J.njobs;
     for (int it = blockIdx.x; it < total && !failed; it += gridDim.x, ++nitem) {
@@ -247,9 +251,11 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
       }
       last_link = nitem;
       // the item's colour vectors, G per stage
+      // spinors are read (and, by the consumers, written) only after the
+      // previous kernel in the stream has completed; links do not depend on it
+      if (nitem == 0) ptx::wait_dependencies();
       const PsiT* base_t = static_cast<const PsiT*>(J.j[job].in) + (size_t)p.t * NC * V3;
-      for (int j = 0; j < SPI; ++j, ++gstage) {
-        const int s = gstage % S, n = gstage / S;
+      for (int j = 0; j < SPI; ++j, ++gstage, s = s + 1 == S ? 0 : s + 1, n += s == 0) {
         if (n > 0) {
           const bool ok = ptx::mbar_wait_bounded(empty0 + 8 * s, (n - 1) & 1, timeout_ns);
           if (!__all_sync(0xffffffffu, ok)) {
@@ -318,7 +324,7 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
   const int lyb = yh ? lk_YH + x : NE * kLx + (r == 0 ? k - 1 : r - 1) * Lx + x;
   const int lyb_stride = yh ? Lx : kLx;
 
-  int gstage = 0, nitem = 0;
+  int s = 0, n = 0, nitem = 0;  // slot and round of the current stage
   const int total = tt.nitems * J.njobs;
   for (int it = blockIdx.x; it < total; it += gridDim.x, ++nitem) {
     const int job = it / tt.nitems;
@@ -341,11 +347,11 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
     }
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(lempty);
+    if (nitem == 0) ptx::wait_dependencies();  // before the first spinor store
 
     const int s3 = x + Lx * ((p.y0 + r) + Ly * p.z);
     PsiT* outp = static_cast<PsiT*>(J.j[job].out) + (size_t)p.t * NC * V3 + s3;
-    for (int j = 0; j < SPI; ++j, ++gstage) {
-      const int s = gstage % S, n = gstage / S;
+    for (int j = 0; j < SPI; ++j, s = s + 1 == S ? 0 : s + 1, n += s == 0) {
       ok = ptx::mbar_wait_bounded(full0 + 8 * s, n & 1, timeout_ns);
       if (!__all_sync(0xffffffffu, ok)) {
         if (lane == 0) atomicOr(status, kStatusFullWait);
@@ -393,9 +399,19 @@ int launch_tma_t(const HopLaunch& a) {
   auto kern = smear_hop_tma_kernel<PsiT, LMODE, LX, KR, HALO, G>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, a.tt.smem);
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "gauss_smear: smem attribute: %s", cudaGetErrorString(e));
-  dim3 block(32 * (a.tt.cwarps + 1));
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.tt.grid);
+  cfg.blockDim = dim3(32 * (a.tt.cwarps + 1));
+  cfg.dynamicSmemBytes = a.tt.smem;
+  cfg.stream = a.stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   ProfScope prof("smear_hop", a.stream);
-  kern<<<a.tt.grid, block, a.tt.smem, a.stream>>>(a.jobs, a.g, a.tt, a.status, a.timeout_ns, a.drop_stage);
+  e = cudaLaunchKernelEx(&cfg, kern, a.jobs, a.g, a.tt, a.status, a.timeout_ns, a.drop_stage);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "gauss_smear hop (pipelined): %s", cudaGetErrorString(e));
   return check_launch("gauss_smear hop (pipelined)");
 }
 
