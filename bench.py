@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true",
                     help="skip the launch-shape autotuning (default shapes; for profiling runs)")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the 64-job batched comparison (FP32 one job at a time vs batched FP32/BF16)")
+    ap.add_argument("--batch-steps", type=int, default=5)
     return ap.parse_args()
 
 
@@ -239,6 +242,130 @@ def traffic_for(kernel: str):
     return None
 
 
+def batch_arms(q, dev, args) -> dict:
+    """The 64 uneven smearing + meson jobs three ways on the same inputs:
+    FP32 one job at a time (gauss_smear + meson_2pt per job), FP32 as one
+    batch replayed from a CUDA graph, and BF16 storage with BF16
+    reconstruct-12 links as one batch from a graph.  Each pass re-imports
+    every propagator, smears it with its own (kappa, N) and contracts the 16
+    zero-momentum mesons.  Returns times, throughput and the BF16 error."""
+    import torch
+
+    from synth import configs, device as synth_dev
+
+    w = configs.BATCH_64
+    jobs = configs.batch_jobs(w)
+    lats, rows = {}, []
+    for j in jobs:
+        dims = j["dims"]
+        if dims not in lats:
+            lats[dims] = q.Lattice(dims, 3)
+        lat = lats[dims]
+        U_can = synth_dev.gauge_field(dims, j["seed"], dev)
+        P_can = synth_dev.propagator(dims, j["seed"], dev)
+        r = {"job": j, "lat": lat, "P": P_can,
+             "U32": q.Field(lat, q.GAUGE, q.F32, device=dev).import_(U_can),
+             "Ub": q.Field(lat, q.GAUGE, q.BF16_R12, device=dev).import_(U_can)}
+        del U_can
+        for tag, prec in (("32", q.F32), ("b", q.BF16)):
+            r["p" + tag] = q.Field(lat, q.PROPAGATOR, prec, device=dev)
+            r["s" + tag] = r["p" + tag].like()
+        r["m1"] = torch.zeros((16, 1, lat.Nt), dtype=torch.complex128, device=dev)
+        r["m32"] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
+        r["mb"] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
+        rows.append(r)
+    # launch shapes per (lattice, precision) class, by the autotuner
+    if not args.no_tune:
+        seen = set()
+        for r in rows:
+            for tag, U in (("32", r["U32"]), ("b", r["Ub"])):
+                key = (r["job"]["dims"], tag)
+                if key not in seen:
+                    seen.add(key)
+                    q.tune_smear(U, r["p" + tag].import_(r["P"]), r["s" + tag], 3, reps=2)
+    b32 = q.Batch([(r["U32"], r["p32"], r["s32"], r["job"]["kappa"], r["job"]["n_iter"], r["m32"]) for r in rows])
+    bb = q.Batch([(r["Ub"], r["pb"], r["sb"], r["job"]["kappa"], r["job"]["n_iter"], r["mb"]) for r in rows])
+
+    def single_fp32():
+        for r in rows:
+            j = r["job"]
+            r["p32"].import_(r["P"])
+            q.gauss_smear(r["U32"], r["p32"], j["kappa"], j["n_iter"], 3, scratch=r["s32"])
+            q.meson_2pt(r["p32"], r["p32"], q.SIXTEEN_MESONS, out=r["m1"])
+
+    def batched(bt, tag):
+        for r in rows:
+            r["p" + tag].import_(r["P"])
+        bt.run(use_graph=True)
+
+    def timed(fn):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.batch_steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        q.device_status()
+        return e0.elapsed_time(e1) / args.batch_steps
+
+    t_single = timed(single_fp32)
+    t_b32 = timed(lambda: batched(b32, "32"))
+    t_bb = timed(lambda: batched(bb, "b"))
+
+    # correlator error of the BF16 batch against FP32, per job: max over
+    # channels of ||C_bf16(.) - C_f32(.)|| / ||C_f32(.)|| over t
+    def corr_err(a, ref):
+        d = torch.linalg.vector_norm(a - ref, dim=-1)
+        n = torch.linalg.vector_norm(ref, dim=-1)
+        n = torch.where(n > 1e-12 * n.max(), n, n.max())
+        return float((d / n).max())
+
+    errs = [corr_err(r["mb"], r["m32"]) for r in rows]
+    # FP32 one at a time and FP32 batched run the same per-site arithmetic:
+    # the smeared fields agree bit for bit (the correlators only to the
+    # order of their FP64 atomic timeslice sums)
+    single_fields = []
+    for r in rows:
+        j = r["job"]
+        r["p32"].import_(r["P"])
+        q.gauss_smear(r["U32"], r["p32"], j["kappa"], j["n_iter"], 3, scratch=r["s32"])
+        q.meson_2pt(r["p32"], r["p32"], q.SIXTEEN_MESONS, out=r["m1"])
+        single_fields.append(r["p32"].storage.clone())
+    batched(b32, "32")
+    torch.cuda.synchronize()
+    same = all(torch.equal(f, r["p32"].storage) for f, r in zip(single_fields, rows))
+    del single_fields
+    mes_dev = max(corr_err(r["m1"][:, 0, :], r["m32"]) for r in rows)
+    by_n = {}
+    for r, e in zip(rows, errs):
+        band = "N<=25" if r["job"]["n_iter"] <= 25 else "N>25"
+        by_n[band] = max(by_n.get(band, 0.0), e)
+    hop_sites = sum(r["job"]["n_iter"] * r["lat"].V for r in rows)
+    sites = sum(r["lat"].V for r in rows)
+    # FP32-equivalent algorithmic bytes of a pass: import, N hops, mesons
+    bytes32 = sum(r["lat"].V * (2 * 1152 + r["job"]["n_iter"] * (2 * 1152 + 216) + 1152) for r in rows)
+    return {
+        "workload": w.name, "jobs": len(rows),
+        "lattices": {f"{d[0]}^3x{d[3]}": sum(1 for r in rows if r["job"]["dims"] == d) for d in lats},
+        "hop_sites_per_pass": hop_sites, "contraction_sites_per_pass": sites,
+        "ms_per_pass": {"fp32_single": t_single, "fp32_batched_graph": t_b32, "bf16_batched_graph": t_bb},
+        "fp32_equiv_gbs": {"fp32_single": bytes32 / t_single / 1e6, "fp32_batched_graph": bytes32 / t_b32 / 1e6,
+                           "bf16_batched_graph": bytes32 / t_bb / 1e6},
+        "speedup_bf16_batched_vs_fp32_single": t_single / t_bb,
+        "speedup_fp32_batched_vs_fp32_single": t_single / t_b32,
+        "bf16_vs_fp32_corr_rel_err_max": max(errs), "bf16_vs_fp32_corr_rel_err_max_by_n": by_n,
+        "bf16_tol": 2e-2, "bf16_within_tol": max(errs) <= 2e-2,
+        "bf16_jobs_err": sorted([[r["job"]["dims"][0], r["job"]["n_iter"], round(e, 5)] for r, e in zip(rows, errs)],
+                                key=lambda x: x[1]),
+        "fp32_batched_fields_equal_single_bitwise": bool(same),
+        "fp32_batched_vs_single_corr_rel_diff": mes_dev,
+        "inputs": "device-generated seeded Haar SU(3) links and exp(-0.5|x|) Gaussian propagators per job",
+    }
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -305,8 +432,6 @@ def gpu_arm(args):
         gpu_id = str(local)
     clocks = ClockSampler(gpu_id)
     clocks.start()
-    q.profile_reset()
-    q.profile_enable(True)
     launches0 = q.launch_count()
     barrier()
     torch.cuda.synchronize()
@@ -318,9 +443,19 @@ def gpu_arm(args):
     torch.cuda.synchronize()
     barrier()
     launches = q.launch_count() - launches0
-    q.profile_enable(False)
     clk = clocks.stop()
     ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+
+    # Per-kernel durations from CUDA events around every launch, in a
+    # separate pass of the same steps: the events between launches keep
+    # consecutive hops from overlapping their set-up, so the step time above
+    # is taken without them.
+    q.profile_reset()
+    q.profile_enable(True)
+    for _ in range(args.steps):
+        step_device()
+    torch.cuda.synchronize()
+    q.profile_enable(False)
     kern = {name: q.profile_query(name) for name in ("smear_hop", "meson_2pt", "field_import", "point_source")}
 
     b = step_bytes(w)
@@ -376,6 +511,11 @@ def gpu_arm(args):
         h2d = U_h.numel() * U_h.element_size() + P_h.numel() * P_h.element_size()
         e2e = {"value": world * b["total"] / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": C_h.numel() * C_h.element_size(), "ms_per_step": e2e_s * 1e3}
+
+    batch = None
+    if not args.no_batch:
+        batch = batch_arms(q, dev, args)
+        components["batch"] = batch
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -64,3 +64,27 @@ SCALE_48x96 = Workload("scale_48^3x96_8props", (48, 48, 48, 96), "near_unit", 0.
                        extra={"kappa_n": ((0.15, 10), (0.20, 20), (0.25, 40), (0.30, 80))})
 
 ALL = (CHAIN_4x8, MESONS_16x32, BF16_24x48, BATCH_64, SCALE_48x96)
+
+
+def batch_jobs(w: Workload = BATCH_64) -> list[dict]:
+    """The jobs of a batched workload: lattice drawn uniformly from
+    ``extra['sizes']``, N uniform in ``extra['n_range']`` (inclusive) and kappa
+    uniform in ``extra['kappa_range']``, from the workload's seeded stream;
+    each job gets its own seed for its fields."""
+    import numpy as np
+
+    from synth import rng
+
+    n = w.extra["n_jobs"]
+    sizes = w.extra["sizes"]
+    n_lo, n_hi = w.extra["n_range"]
+    k_lo, k_hi = w.extra["kappa_range"]
+    key = rng.stream_key(w.seed, 90)
+    u = rng.uniform(key, np.arange(3 * n, dtype=np.uint64)).reshape(n, 3)
+    jobs = []
+    for j in range(n):
+        jobs.append({"dims": tuple(sizes[min(int(u[j, 0] * len(sizes)), len(sizes) - 1)]),
+                     "n_iter": n_lo + min(int(u[j, 1] * (n_hi - n_lo + 1)), n_hi - n_lo),
+                     "kappa": k_lo + (k_hi - k_lo) * float(u[j, 2]),
+                     "seed": w.seed * 100 + j})
+    return jobs
