@@ -366,6 +366,24 @@ def batch_arms(q, dev, args) -> dict:
     }
 
 
+def max_over_ranks(x: float, world: int, device) -> float:
+    """Largest per-rank value (the slowest rank's time) on every rank."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world: int, units_per_rank: float, seconds: float) -> float:
+    """Units all ranks processed (each rank its own problem of the same size)
+    divided by the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 def gpu_arm(args):
     import numpy as np
     import torch
@@ -413,13 +431,6 @@ def gpu_arm(args):
         if world > 1:
             dist.barrier()
 
-    def max_over_ranks(x: float) -> float:
-        if world == 1:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         step_device()
@@ -444,7 +455,7 @@ def gpu_arm(args):
     barrier()
     launches = q.launch_count() - launches0
     clk = clocks.stop()
-    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps)
+    ms = max_over_ranks(ev0.elapsed_time(ev1) / args.steps, world, dev)
 
     # Per-kernel durations from CUDA events around every launch, in a
     # separate pass of the same steps: the events between launches keep
@@ -460,7 +471,7 @@ def gpu_arm(args):
 
     b = step_bytes(w)
     peaks = measured_peaks()
-    value = world * b["total"] / (ms * 1e-3) / 1e9
+    value = whole_job_rate(world, b["total"], ms * 1e-3) / 1e9
 
     hop_ms, hop_n = kern["smear_hop"]
     hop_avg_s = hop_ms / hop_n * 1e-3
@@ -507,9 +518,9 @@ def gpu_arm(args):
         for _ in range(args.steps):
             step_e2e()
         barrier()
-        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps)
+        e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
         h2d = U_h.numel() * U_h.element_size() + P_h.numel() * P_h.element_size()
-        e2e = {"value": world * b["total"] / e2e_s / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+        e2e = {"value": whole_job_rate(world, b["total"], e2e_s) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": C_h.numel() * C_h.element_size(), "ms_per_step": e2e_s * 1e3}
 
     batch = None
