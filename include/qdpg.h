@@ -41,6 +41,24 @@
  *    QDPG_FERMION      12    comp = s*3 + c
  *    QDPG_PROPAGATOR  144    comp = (s*3 + c)*12 + (s'*3 + c')  (sink s,c; source s',c')
  *
+ *  QDPG_F16 propagators (the reduced-precision storage of the smearing and
+ *  contraction path) are stored site-major instead, so that the tensor-core
+ *  smearing kernel reads each site's colour vectors contiguously.  With
+ *  v = s*12 + s'*3 + c' (the 48 colour vectors of a site) and c the sink
+ *  colour, the float16 pair of (t, comp, s3) is word
+ *
+ *      ((t*3 + v/16) * V3 + s3) * 48 + (v%16)*3 + c
+ *
+ *  (three groups of 16 vectors, each group site-major).  The represented
+ *  value is the stored pair times 2^exp, where exp is a per-field scale that
+ *  keeps the stored numbers inside the float16 range while smearing grows
+ *  the field by up to (1 + 6 kappa) per iteration.  exp and the largest
+ *  stored magnitude live in a scale record of QDPG_F16_RECORD_BYTES bytes
+ *  placed after the data, at byte offset round_up(V*144*4, 256); the record
+ *  is part of the field (qdpg_field_bytes includes it) and every operation
+ *  on the field reads or updates it on the device.  F16 gauge fields need
+ *  no scale (|U_ab| <= 1) and use the component-major layout above.
+ *
  *  Canonical layout (import/export): complex numbers, site index
  *  x0 + L0*(x1 + L1*(x2 + L2*x3)); propagator/fermion/colour matrix are
  *  [site][comp] with the comp order above; the gauge field is
@@ -81,8 +99,16 @@ typedef enum {
   QDPG_F32 = 0,       /* complex float32 (float2) */
   QDPG_BF16 = 1,      /* complex bfloat16 pair */
   QDPG_F32_R12 = 2,   /* gauge only: float2, two rows stored */
-  QDPG_BF16_R12 = 3   /* gauge only: bfloat16 pair, two rows stored */
+  QDPG_BF16_R12 = 3,  /* gauge only: bfloat16 pair, two rows stored */
+  QDPG_F16 = 4,       /* complex float16 pair; propagator or gauge (layout notes above) */
+  QDPG_F16_R12 = 5    /* gauge only: float16 pair, two rows stored */
 } qdpg_prec;
+
+/* Size of the scale record of a QDPG_F16 propagator (see the layout notes):
+ * int32 exp, float max |stored|, then the per-iteration scale slots of a
+ * smearing call (at most QDPG_F16_MAX_ITER iterations per call). */
+#define QDPG_F16_RECORD_BYTES 8192
+#define QDPG_F16_MAX_ITER 999
 
 typedef enum {
   QDPG_CANON_F64 = 0, /* canonical buffer of complex double (2 x double) */
@@ -130,14 +156,17 @@ int qdpg_device_status(void* stream);
  * and launch-shape settings of the pipelined smearing kernel:
  *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..256, 0 = default;
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
- *  QDPG_TUNE_GRID              0: persistent CTAs (default), 1: one CTA per item. */
+ *  QDPG_TUNE_GRID              0: persistent CTAs (default), 1: one CTA per item;
+ * and of the float16 (tensor-core) smearing kernel:
+ *  QDPG_TUNE_F16_WARPS         consumer warps per CTA, 8 or 16 (0 = default, 16). */
 enum {
   QDPG_DEBUG_WAIT_TIMEOUT_NS = 1,
   QDPG_DEBUG_DROP_STAGE = 2,
   QDPG_DEBUG_FORCE_SIMPLE_HOP = 3,
   QDPG_TUNE_TILE_CONSUMERS = 4,
   QDPG_TUNE_STAGES = 5,
-  QDPG_TUNE_GRID = 7
+  QDPG_TUNE_GRID = 7,
+  QDPG_TUNE_F16_WARPS = 8
 };
 int qdpg_debug_set(int what, long long value);
 

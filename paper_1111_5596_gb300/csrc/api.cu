@@ -33,22 +33,27 @@ int check_launch(const char* what) {
   return QDPG_OK;
 }
 
-bool is_r12(int prec) { return prec == QDPG_F32_R12 || prec == QDPG_BF16_R12; }
+bool is_r12(int prec) { return prec == QDPG_F32_R12 || prec == QDPG_BF16_R12 || prec == QDPG_F16_R12; }
 bool is_bf16(int prec) { return prec == QDPG_BF16 || prec == QDPG_BF16_R12; }
+bool is_f16(int prec) { return prec == QDPG_F16 || prec == QDPG_F16_R12; }
 
 int esize_of(int prec) {
   switch (prec) {
     case QDPG_F32:
     case QDPG_F32_R12: return 8;
     case QDPG_BF16:
-    case QDPG_BF16_R12: return 4;
+    case QDPG_BF16_R12:
+    case QDPG_F16:
+    case QDPG_F16_R12: return 4;
     default: return 0;
   }
 }
 
 int ncomp_of(int kind, int prec) {
-  if (prec < QDPG_F32 || prec > QDPG_BF16_R12) return 0;
+  if (prec < QDPG_F32 || prec > QDPG_F16_R12) return 0;
   if (is_r12(prec) && kind != QDPG_GAUGE) return 0;
+  // float16 storage: propagators (scaled, site-major) and gauge links only
+  if (prec == QDPG_F16 && kind != QDPG_PROPAGATOR && kind != QDPG_GAUGE) return 0;
   switch (kind) {
     case QDPG_COLOR_MATRIX: return 9;
     case QDPG_GAUGE: return is_r12(prec) ? 24 : 36;
@@ -111,6 +116,7 @@ size_t qdpg_field_bytes(qdpg_lattice_t lat, int kind, int prec) {
   if (!lat) return 0;
   int nc = ncomp_of(kind, prec);
   if (!nc) return 0;
+  if (kind == QDPG_PROPAGATOR && prec == QDPG_F16) return f16_data_bytes(lat->g.V) + QDPG_F16_RECORD_BYTES;
   return (size_t)lat->g.V * (size_t)nc * (size_t)esize_of(prec);
 }
 
@@ -132,6 +138,9 @@ int qdpg_field_wrap(qdpg_lattice_t lat, int kind, int prec, void* dev_ptr, size_
   f->esize = esize_of(prec);
   f->data = dev_ptr;
   f->bytes = bytes;
+  f->rec = (kind == QDPG_PROPAGATOR && prec == QDPG_F16)
+               ? reinterpret_cast<ScaleRecord*>(static_cast<char*>(dev_ptr) + f16_data_bytes(lat->g.V))
+               : nullptr;
   *out = f;
   return ok();
 }

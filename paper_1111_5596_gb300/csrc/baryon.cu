@@ -20,6 +20,8 @@
 // in shared memory (coalesced loads); each warp then contracts one site at
 // a time, its lanes splitting the 36 (eps, eps') colour terms x Wick terms.
 // Site values are FP32; timeslice/momentum sums are FP64.
+#include <cuda_fp16.h>
+
 #include <vector>
 
 #include "gamma_host.h"
@@ -60,6 +62,17 @@ __device__ __forceinline__ float2 caddf(float2 a, float2 b) { return make_float2
 
 __device__ __forceinline__ float2 ldb(const float2* p) { return __ldg(p); }
 __device__ __forceinline__ float2 ldb(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
+__device__ __forceinline__ float2 ldb(const __half2* p) { return __half22float2(*p); }
+// Element (t, comp, s3) of a propagator: component-major (F32, BF16) or
+// site-major float16 (qdpg.h).
+template <typename PsiT>
+__device__ __forceinline__ long long prop_off(int V3, int t, int comp, int s3) {
+  return ((long long)t * 144 + comp) * V3 + s3;
+}
+template <>
+__device__ __forceinline__ long long prop_off<__half2>(int V3, int t, int comp, int s3) {
+  return f16_prop_index(V3, t, comp, s3);
+}
 
 // spin block S^{c c'}: element (al, alp) of the staged site
 __device__ __forceinline__ void load_block(const float2* S, int c, int cp, float2 A[16]) {
@@ -202,7 +215,8 @@ __device__ __forceinline__ float2 baryon_term(const BaryonSpec& B, const float2*
 template <typename PsiT, int KIND, bool SITES>
 __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restrict__ Su, const PsiT* __restrict__ Sd,
                                                              Geom g, BaryonSpec B, BMoms M, double* __restrict__ out,
-                                                             float2* __restrict__ sites) {
+                                                             float2* __restrict__ sites, const ScaleRecord* ru,
+                                                             const ScaleRecord* rd) {
   extern __shared__ float2 sm[];
   float2* su = sm;
   float2* sd = sm + kSites * kStride;
@@ -211,6 +225,8 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
   const int s0 = blockIdx.x * kSites;
   const int V3 = g.V3;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // float16 storage: the value is the stored number times 2^exp (u, u, d)
+  const int scale_exp = ru ? 2 * ru->exp + rd->exp : 0;
 
   // stage the two propagators of the block's sites ([site][comp], padded)
   for (int e = threadIdx.x; e < 144 * kSites; e += blockDim.x) {
@@ -218,7 +234,7 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
     const int s3 = s0 + i;
     float2 vu = make_float2(0.f, 0.f), vd = make_float2(0.f, 0.f);
     if (s3 < V3) {
-      const long long off = ((long long)t * 144 + comp) * V3 + s3;
+      const long long off = prop_off<PsiT>(V3, t, comp, s3);
       vu = ldb(Su + off);
       vd = ldb(Sd + off);
     }
@@ -241,7 +257,9 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
       acc.y += __shfl_down_sync(0xffffffffu, acc.y, o);
     }
     if constexpr (SITES) {
-      if (lane == 0) sites[(long long)t * V3 + s3] = acc;
+      if (lane == 0)
+        sites[(long long)t * V3 + s3] =
+            scale_exp ? make_float2(ldexpf(acc.x, scale_exp), ldexpf(acc.y, scale_exp)) : acc;
       continue;
     }
     if (lane == 0) {
@@ -273,8 +291,8 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
       im += red[w * M.n + m].y;
     }
     const long long o = (long long)m * g.Nt + t;
-    atomicAdd(out + 2 * o, re);
-    atomicAdd(out + 2 * o + 1, im);
+    atomicAdd(out + 2 * o, ldexp(re, scale_exp));
+    atomicAdd(out + 2 * o + 1, ldexp(im, scale_exp));
   }
 }
 
@@ -297,8 +315,8 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
   }
   if (Su->kind != QDPG_PROPAGATOR || Sd->kind != QDPG_PROPAGATOR)
     return fail(QDPG_ERR_SHAPE, "baryon_2pt: Su and Sd must be propagators");
-  if ((Su->prec != QDPG_F32 && Su->prec != QDPG_BF16) || Sd->prec != Su->prec)
-    return fail(QDPG_ERR_DTYPE, "baryon_2pt: Su and Sd must share F32 or BF16 storage");
+  if ((Su->prec != QDPG_F32 && Su->prec != QDPG_BF16 && Su->prec != QDPG_F16) || Sd->prec != Su->prec)
+    return fail(QDPG_ERR_DTYPE, "baryon_2pt: Su and Sd must share F32, BF16 or F16 storage");
   for (int mu = 0; mu < 4; ++mu)
     if (Su->g.L[mu] != Sd->g.L[mu] || Su->g.jd != Sd->g.jd) return fail(QDPG_ERR_SHAPE, "baryon_2pt: lattices differ");
   if (n_mom < 1 || n_mom > kMaxMomB) return fail(QDPG_ERR_ARG, "baryon_2pt: n_mom %d outside 1..%d", n_mom, kMaxMomB);
@@ -351,17 +369,20 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
       auto k = baryon_kernel<T, KIND, true>;                                                                 \
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
       k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, \
-                                        M, out_dev, sites);                                                  \
+                                        M, out_dev, sites, Su->rec, Sd->rec);                                \
     } else {                                                                                                 \
       auto k = baryon_kernel<T, KIND, false>;                                                                \
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
       k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, \
-                                        M, out_dev, sites);                                                  \
+                                        M, out_dev, sites, Su->rec, Sd->rec);                                \
     }                                                                                                        \
   } while (0)
   if (Su->prec == QDPG_BF16) {
     if (kind == 0) QDPG_BARYON_LAUNCH(__nv_bfloat162, 0);
     else QDPG_BARYON_LAUNCH(__nv_bfloat162, 1);
+  } else if (Su->prec == QDPG_F16) {
+    if (kind == 0) QDPG_BARYON_LAUNCH(__half2, 0);
+    else QDPG_BARYON_LAUNCH(__half2, 1);
   } else {
     if (kind == 0) QDPG_BARYON_LAUNCH(float2, 0);
     else QDPG_BARYON_LAUNCH(float2, 1);

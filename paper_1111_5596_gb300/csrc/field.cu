@@ -3,6 +3,8 @@
 // Source creation is the first stage of the paper's Chroma measurement
 // (Sec. 5); shift is the nearest-neighbour primitive of QDP++ expressions
 // (Sec. 1).  All kernels here are pure data movement.
+#include <cuda_fp16.h>
+
 #include "qdpg_internal.h"
 #include "qdpg_profile.h"
 
@@ -28,6 +30,14 @@ __device__ __forceinline__ void store_elem(__nv_bfloat162* p, double re, double 
   v.x = __double2bfloat16(re);
   v.y = __double2bfloat16(im);
   *p = v;
+}
+__device__ __forceinline__ void store_elem(__half2* p, double re, double im) {
+  *p = __halves2half2(__double2half(re), __double2half(im));
+}
+__device__ __forceinline__ void load_elem(const __half2* p, double& re, double& im) {
+  const float2 v = __half22float2(*p);
+  re = v.x;
+  im = v.y;
 }
 __device__ __forceinline__ void load_elem(const float2* p, double& re, double& im) {
   float2 v = *p;
@@ -161,6 +171,123 @@ __global__ void __launch_bounds__(kThreads) shift_kernel(T* __restrict__ dst, co
   }
 }
 
+// ---- float16 propagators: site-major layout with a power-of-two scale ---------
+//
+// The canonical component comp = (s*3 + c)*12 + s' * 3 + c' of device word
+// i (decomposed as in f16_prop_index, qdpg_internal.h).
+__device__ __forceinline__ void f16_word_decode(long long i, int V3, int& t, int& s3, int& comp) {
+  const int w = (int)(i % 48);
+  const long long r = i / 48;
+  s3 = (int)(r % V3);
+  const long long r2 = r / V3;
+  const int vg = (int)(r2 % 3);
+  t = (int)(r2 / 3);
+  const int v = vg * 16 + w / 3, c = w % 3;
+  const int s = v / 12, sp = v - 12 * s;
+  comp = (s * 3 + c) * 12 + sp;
+}
+
+// Exponent e with m * 2^-e < 2^14 (0 for m = 0).
+__device__ __forceinline__ int f16_exp_for(float m) {
+  if (!(m > 0.f)) return 0;
+  int ex;
+  frexpf(m, &ex);  // m = f * 2^ex, f in [0.5, 1)
+  return ex - 14;
+}
+
+template <typename Src>
+__global__ void __launch_bounds__(kThreads) f16_max_kernel(const Src* __restrict__ src, long long n,
+                                                           unsigned* __restrict__ out) {
+  float m = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    m = fmaxf(m, __double2float_ru(fmax(fabs((double)src[i]), 0.0)));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
+}
+
+template <typename Src>
+__global__ void __launch_bounds__(kThreads) f16_import_kernel(__half2* __restrict__ dst, const Src* __restrict__ src,
+                                                              Geom g, ScaleRecord* rec) {
+  const float m = __uint_as_float(rec->tmpmax);
+  const int e = f16_exp_for(m);
+  const long long total = g.V * 144;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int t, s3, comp;
+    f16_word_decode(i, g.V3, t, s3, comp);
+    const long long ci = canon_site(g, t, s3) * 144 + comp;
+    store_elem(dst + i, ldexp((double)src[2 * ci], -e), ldexp((double)src[2 * ci + 1], -e));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    rec->exp = e;
+    rec->maxabs = ldexpf(m, -e) * (1.f + 1.f / 1024.f);  // bound after rounding to float16
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) f16_export_kernel(double* __restrict__ out, const __half2* __restrict__ dev,
+                                                              Geom g, const ScaleRecord* rec) {
+  const int e = rec->exp;
+  const long long total = g.V * 144;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int t, s3, comp;
+    f16_word_decode(i, g.V3, t, s3, comp);
+    const long long ci = canon_site(g, t, s3) * 144 + comp;
+    double re, im;
+    load_elem(dev + i, re, im);
+    out[2 * ci] = ldexp(re, e);
+    out[2 * ci + 1] = ldexp(im, e);
+  }
+}
+
+// Unit entries of a point source at (t, s3); the data was zeroed before.
+__global__ void f16_point_kernel(__half2* __restrict__ f, int V3, int t, int s3, ScaleRecord* rec) {
+  const int k = threadIdx.x;
+  if (k < 12) f[f16_prop_index(V3, t, k * 13, s3)] = __halves2half2(__float2half(1.f), __float2half(0.f));
+  if (k == 0) {
+    rec->exp = 0;
+    rec->maxabs = 1.f;
+  }
+}
+
+// dst(x) = src(x + sign mu_hat) on whole 48-word site blocks; copies the scale.
+__global__ void __launch_bounds__(kThreads) f16_shift_kernel(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src,
+                                                             Geom g, int mu, int sign, ScaleRecord* drec,
+                                                             const ScaleRecord* srec) {
+  const long long total = g.V * 144;
+  int k = -1;
+  for (int d = 0; d < 3; ++d)
+    if (g.sd[d] == mu) k = d;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int w = (int)(i % 48);
+    const long long r = i / 48;
+    const int s3 = (int)(r % g.V3);
+    const long long r2 = r / g.V3;
+    const int vg = (int)(r2 % 3);
+    const int t = (int)(r2 / 3);
+    int t2 = t, s32 = s3;
+    if (k < 0) {
+      t2 = t + sign;
+      t2 = t2 < 0 ? t2 + g.Nt : (t2 >= g.Nt ? t2 - g.Nt : t2);
+    } else {
+      int c[3];
+      c[0] = s3 % g.sL[0];
+      c[1] = (s3 / g.sL[0]) % g.sL[1];
+      c[2] = s3 / (g.sL[0] * g.sL[1]);
+      const int v = c[k] + sign;
+      c[k] = v < 0 ? v + g.sL[k] : (v >= g.sL[k] ? v - g.sL[k] : v);
+      s32 = c[0] + g.sL[0] * (c[1] + g.sL[1] * c[2]);
+    }
+    dst[i] = src[(((long long)t2 * 3 + vg) * g.V3 + s32) * 48 + w];
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    drec->exp = srec->exp;
+    drec->maxabs = srec->maxabs;
+  }
+}
+
 }  // namespace
 
 }  // namespace qdpg
@@ -177,8 +304,34 @@ int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* 
   const long long total = dst->g.V * dst->ncomp;
   const bool r12 = is_r12(dst->prec);
   const int grid = grid_for(total);
+  if (is_f16_prop(dst)) {
+    // largest |re|, |im| first: it fixes the power-of-two scale of the data
+    cudaError_t e = cudaMemsetAsync(&dst->rec->tmpmax, 0, sizeof(unsigned), s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "field_import: memset: %s", cudaGetErrorString(e));
+    ProfScope prof("field_import", s);
+    auto* d = static_cast<__half2*>(dst->data);
+    if (canon == QDPG_CANON_F64) {
+      f16_max_kernel<<<grid_for(2 * total), kThreads, 0, s>>>(static_cast<const double*>(canon_dev), 2 * total,
+                                                              &dst->rec->tmpmax);
+      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->rec);
+    } else {
+      f16_max_kernel<<<grid_for(2 * total), kThreads, 0, s>>>(static_cast<const float*>(canon_dev), 2 * total,
+                                                              &dst->rec->tmpmax);
+      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->rec);
+    }
+    count_launches(1);
+    return check_launch("field_import");
+  }
   ProfScope prof("field_import", s);
-  if (is_bf16(dst->prec)) {
+  if (is_f16(dst->prec)) {
+    auto* d = static_cast<__half2*>(dst->data);
+    if (canon == QDPG_CANON_F64)
+      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
+                                                      r12, dst->ncomp);
+    else
+      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
+                                                     r12, dst->ncomp);
+  } else if (is_bf16(dst->prec)) {
     auto* d = static_cast<__nv_bfloat162*>(dst->data);
     if (canon == QDPG_CANON_F64)
       import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
@@ -205,7 +358,12 @@ int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream) {
   const int grid = grid_for(total);
   const bool r12 = is_r12(src->prec);
   ProfScope prof("field_export", s);
-  if (is_bf16(src->prec))
+  if (is_f16_prop(src))
+    f16_export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->rec);
+  else if (is_f16(src->prec))
+    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->kind,
+                                            r12, src->ncomp);
+  else if (is_bf16(src->prec))
     export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __nv_bfloat162*>(src->data), src->g,
                                             src->kind, r12, src->ncomp);
   else
@@ -218,14 +376,23 @@ int qdpg_point_source(qdpg_field_t f, const int x0[4], int spin_color, void* str
   if (!f || !x0) return fail(QDPG_ERR_ARG, "point_source: null argument");
   if (f->kind != QDPG_PROPAGATOR && f->kind != QDPG_FERMION)
     return fail(QDPG_ERR_SHAPE, "point_source: field must be a propagator or fermion");
-  if (f->prec != QDPG_F32 && f->prec != QDPG_BF16)
-    return fail(QDPG_ERR_DTYPE, "point_source: storage must be F32 or BF16");
+  if (f->prec != QDPG_F32 && f->prec != QDPG_BF16 && f->prec != QDPG_F16)
+    return fail(QDPG_ERR_DTYPE, "point_source: storage must be F32, BF16 or F16");
   for (int mu = 0; mu < 4; ++mu)
     if (x0[mu] < 0 || x0[mu] >= f->g.L[mu]) return fail(QDPG_ERR_ARG, "point_source: x0[%d] outside lattice", mu);
   if (f->kind == QDPG_FERMION && (spin_color < 0 || spin_color > 11))
     return fail(QDPG_ERR_ARG, "point_source: spin_color %d outside 0..11", spin_color);
   cudaStream_t s = as_stream(stream);
   const Geom& g = f->g;
+  if (is_f16_prop(f)) {
+    cudaError_t e = cudaMemsetAsync(f->data, 0, f16_data_bytes(g.V), s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "point_source: memset: %s", cudaGetErrorString(e));
+    const int t = x0[g.jd];
+    const int s3 = x0[g.sd[0]] + g.sL[0] * (x0[g.sd[1]] + g.sL[1] * x0[g.sd[2]]);
+    ProfScope prof("point_source", s);
+    f16_point_kernel<<<1, 32, 0, s>>>(static_cast<__half2*>(f->data), g.V3, t, s3, f->rec);
+    return check_launch("point_source");
+  }
   size_t bytes = (size_t)g.V * f->ncomp * f->esize;
   cudaError_t e = cudaMemsetAsync(f->data, 0, bytes, s);
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "point_source: memset: %s", cudaGetErrorString(e));
@@ -253,7 +420,11 @@ int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* strea
   const long long total = src->g.V * src->ncomp;
   const int grid = grid_for(total);
   ProfScope prof("shift", s);
-  if (src->esize == 8)
+  if (is_f16_prop(src))
+    f16_shift_kernel<<<grid, kThreads, 0, s>>>(static_cast<uint32_t*>(dst->data),
+                                               static_cast<const uint32_t*>(src->data), src->g, mu, sign, dst->rec,
+                                               src->rec);
+  else if (src->esize == 8)
     shift_kernel<<<grid, kThreads, 0, s>>>(static_cast<uint2*>(dst->data), static_cast<const uint2*>(src->data),
                                            src->g, src->ncomp, mu, sign);
   else

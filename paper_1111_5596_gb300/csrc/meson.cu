@@ -21,6 +21,8 @@
 // A thread owns one site.  Site values are FP32; the timeslice/momentum sums
 // are FP64: warp shuffle, then shared memory across warps, then one FP64
 // atomic per block and value.
+#include <cuda_fp16.h>
+
 #include <vector>
 
 #include "qdpg_internal.h"
@@ -59,6 +61,36 @@ __device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
   return __bfloat1622float2(v);
 }
 
+// Element loaders of one site's propagator: component-major (F32, BF16)
+// and site-major float16 (qdpg.h); comp folds to a constant when unrolled.
+template <typename PsiT>
+struct SoASite {
+  const PsiT* p;
+  int V3;
+  __device__ SoASite(const PsiT* S, int t, int s3, int V3_) : p(S + (long long)t * 144 * V3_ + s3), V3(V3_) {}
+  __device__ __forceinline__ float2 operator()(int comp) const { return ld2(p + (long long)comp * V3); }
+};
+struct F16Site {
+  const __half2* p[3];
+  __device__ F16Site(const __half2* S, int t, int s3, int V3) {
+#pragma unroll
+    for (int vg = 0; vg < 3; ++vg) p[vg] = S + ((long long)(t * 3 + vg) * V3 + s3) * 48;
+  }
+  __device__ __forceinline__ float2 operator()(int comp) const {
+    const int sc = comp / 12, sp = comp % 12, sv = sc / 3, c = sc % 3;
+    const int v = sv * 12 + sp;
+    return __half22float2(p[v >> 4][(v & 15) * 3 + c]);
+  }
+};
+template <typename PsiT>
+struct SiteOf {
+  typedef SoASite<PsiT> type;
+};
+template <>
+struct SiteOf<__half2> {
+  typedef F16Site type;
+};
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -70,7 +102,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 template <int NQ, typename PsiT, bool SITES>
 __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __restrict__ S1, const PsiT* __restrict__ S2,
                                                               Geom g, MesonPass P, Moms M, double* __restrict__ out,
-                                                              float2* __restrict__ sites) {
+                                                              float2* __restrict__ sites, const ScaleRecord* rec1,
+                                                              const ScaleRecord* rec2) {
   extern __shared__ double2 red[];  // [warp][nch * n_mom]
   const int s3 = blockIdx.x * kMesonThreads + threadIdx.x;
   const int t = blockIdx.y;
@@ -85,10 +118,10 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
 #pragma unroll
     for (int k = 0; k < 16; ++k) Q[q][k] = make_float2(0.f, 0.f);
 
+  // float16 storage: the value is the stored number times 2^exp per field
+  const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
   if (live) {
-    const long long base = (long long)t * 144 * V3 + s3;
-    const PsiT* p1 = S1 + base;
-    const PsiT* p2 = S2 + base;
+    const typename SiteOf<PsiT>::type p1(S1, t, s3, V3), p2(S2, t, s3, V3);
 #pragma unroll
     for (int al = 0; al < 4; ++al)
 #pragma unroll
@@ -97,7 +130,7 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
 #pragma unroll
         for (int d = 0; d < 3; ++d)
 #pragma unroll
-          for (int b = 0; b < 3; ++b) a[d * 3 + b] = ld2(p1 + (long long)((al * 3 + d) * 12 + be * 3 + b) * V3);
+          for (int b = 0; b < 3; ++b) a[d * 3 + b] = p1((al * 3 + d) * 12 + be * 3 + b);
 #pragma unroll
         for (int q = 0; q < NQ; ++q) {
           const int al2 = al ^ P.ma[q], be2 = be ^ P.mb[q];
@@ -106,7 +139,7 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
           for (int d = 0; d < 3; ++d)
 #pragma unroll
             for (int b = 0; b < 3; ++b) {
-              const float2 y = ld2(p2 + (long long)((al2 * 3 + d) * 12 + be2 * 3 + b) * V3);
+              const float2 y = p2((al2 * 3 + d) * 12 + be2 * 3 + b);
               const float2 x = a[d * 3 + b];
               // acc += x * conj(y)
               acc.x = fmaf(x.x, y.x, acc.x);
@@ -141,7 +174,9 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
         c.y = fmaf(w.y, Q[q][k].x, c.y);
       }
       if constexpr (SITES) {
-        if (live) sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] = c;
+        if (live)
+          sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] =
+              scale_exp ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
       } else {
         for (int m = 0; m < M.n; ++m) {
           float2 v = c;
@@ -177,8 +212,8 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
     }
     const int j = i / M.n, m = i % M.n;
     const long long o = ((long long)P.out_row[j] * M.n + m) * g.Nt + t;
-    atomicAdd(out + 2 * o, re);
-    atomicAdd(out + 2 * o + 1, im);
+    atomicAdd(out + 2 * o, ldexp(re, scale_exp));
+    atomicAdd(out + 2 * o + 1, ldexp(im, scale_exp));
   }
 }
 
@@ -193,19 +228,23 @@ int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const q
   dim3 grid((g.V3 + kMesonThreads - 1) / kMesonThreads, g.Nt);
   const size_t smem = sites ? 0 : (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
   const bool bf = S1->prec == QDPG_BF16;
+  const bool h16 = S1->prec == QDPG_F16;
   ProfScope prof("meson_2pt", s);
 #define QDPG_MESON_KERNEL(NQ, T, SITES)                                                                 \
   do {                                                                                                 \
     auto k = meson_kernel<NQ, T, SITES>;                                                               \
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     k<<<grid, kMesonThreads, smem, s>>>(static_cast<const T*>(S1->data), static_cast<const T*>(S2->data), g, P, M, \
-                                        out, sites);                                                   \
+                                        out, sites, S1->rec, S2->rec);                                 \
   } while (0)
 #define QDPG_MESON_LAUNCH(NQ)                                       \
   do {                                                              \
     if (bf) {                                                       \
       if (sites) QDPG_MESON_KERNEL(NQ, __nv_bfloat162, true);       \
       else QDPG_MESON_KERNEL(NQ, __nv_bfloat162, false);            \
+    } else if (h16) {                                               \
+      if (sites) QDPG_MESON_KERNEL(NQ, __half2, true);              \
+      else QDPG_MESON_KERNEL(NQ, __half2, false);                   \
     } else {                                                        \
       if (sites) QDPG_MESON_KERNEL(NQ, float2, true);               \
       else QDPG_MESON_KERNEL(NQ, float2, false);                    \
@@ -238,8 +277,8 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
     return fail(QDPG_ERR_ARG, "meson_2pt: null argument");
   if (S1->kind != QDPG_PROPAGATOR || S2->kind != QDPG_PROPAGATOR)
     return fail(QDPG_ERR_SHAPE, "meson_2pt: S1 and S2 must be propagators");
-  if ((S1->prec != QDPG_F32 && S1->prec != QDPG_BF16) || S2->prec != S1->prec)
-    return fail(QDPG_ERR_DTYPE, "meson_2pt: S1 and S2 must share F32 or BF16 storage");
+  if ((S1->prec != QDPG_F32 && S1->prec != QDPG_BF16 && S1->prec != QDPG_F16) || S2->prec != S1->prec)
+    return fail(QDPG_ERR_DTYPE, "meson_2pt: S1 and S2 must share F32, BF16 or F16 storage");
   for (int mu = 0; mu < 4; ++mu)
     if (S1->g.L[mu] != S2->g.L[mu] || S1->g.jd != S2->g.jd) return fail(QDPG_ERR_SHAPE, "meson_2pt: lattices differ");
   if (n_chan < 1 || n_chan > 256) return fail(QDPG_ERR_ARG, "meson_2pt: n_chan %d outside 1..256", n_chan);

@@ -30,6 +30,35 @@ struct qdpg_lattice {
   qdpg::Geom g;
 };
 
+namespace qdpg {
+
+// Scale record of a QDPG_F16 propagator (device memory, after the data).
+// The field's value is stored * 2^exp.  cmax/cexp are the per-iteration
+// slots of one smearing call: hop k reads slot k and writes slot k+1.
+constexpr int kScaleSlots = QDPG_F16_MAX_ITER + 1;
+struct ScaleRecord {
+  int exp;            // value = stored * 2^exp
+  float maxabs;       // bound on |re|, |im| of the stored numbers
+  unsigned tmpmax;    // scratch of the import's max reduction (float bits)
+  int pad[13];
+  float cmax[kScaleSlots];
+  int cexp[kScaleSlots];
+};
+static_assert(sizeof(ScaleRecord) <= QDPG_F16_RECORD_BYTES, "scale record too large");
+
+// Word index of (t, comp, s3) in a QDPG_F16 propagator (see qdpg.h).
+__host__ __device__ inline long long f16_prop_index(int V3, int t, int comp, int s3) {
+  const int sc = comp / 12, sp = comp - 12 * sc;  // sink (s, c); source (s', c')
+  const int s = sc / 3, c = sc - 3 * s;
+  const int v = s * 12 + sp;
+  return ((long long)(t * 3 + (v >> 4)) * V3 + s3) * 48 + (v & 15) * 3 + c;
+}
+
+// Bytes of the data part of a field (the scale record follows, 256-aligned).
+inline size_t f16_data_bytes(long long V) { return (((size_t)V * 144 * 4) + 255) / 256 * 256; }
+
+}  // namespace qdpg
+
 struct qdpg_field {
   qdpg::Geom g;
   int kind;
@@ -38,6 +67,7 @@ struct qdpg_field {
   int esize;     // bytes per complex element
   void* data;    // borrowed device pointer
   size_t bytes;  // size of the wrapped buffer
+  qdpg::ScaleRecord* rec;  // F16 propagators: the scale record inside the buffer; else null
 };
 
 namespace qdpg {
@@ -53,6 +83,9 @@ int ncomp_of(int kind, int prec);
 int esize_of(int prec);
 bool is_r12(int prec);
 bool is_bf16(int prec);
+bool is_f16(int prec);
+// A QDPG_F16 propagator: site-major layout with a scale record.
+inline bool is_f16_prop(const qdpg_field* f) { return f->kind == QDPG_PROPAGATOR && f->prec == QDPG_F16; }
 
 // Per-device status word (device address) for bounded-wait timeouts.
 unsigned int* device_status_word();
@@ -62,6 +95,7 @@ bool debug_force_simple_hop();
 int debug_tile_consumers();  // max consumer threads per pipelined tile, 0 = per-geometry default
 int debug_tile_stages();     // pipeline depth, 0 = as many as fit the shared-memory budget
 int debug_tile_grid();       // 0: persistent CTAs, 1: one CTA per work item
+int debug_f16_warps();       // consumer warps of the float16 smearing kernel, 0 = default
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage
 constexpr unsigned int kStatusDrain = 4u;      // producer gave up draining its own copies
@@ -77,6 +111,25 @@ int launch_hop_any(const void* in, void* out, const void* U, int lprec, int psi_
 // (each job its own in/out/links/kappa); QDPG_ERR_UNSUPPORTED as above.
 int launch_hop_tma_batch(const void* const* in, void* const* out, const void* const* U, const float* kappa, int njobs,
                          int lprec, int psi_prec, const Geom& g, const int hop_mu[3], cudaStream_t s);
+
+// Tensor-core smearing hop of float16 propagators (smear_mma.cu): one hop
+// of up to kMaxF16Jobs jobs on the same lattice and link precision (F16 or
+// F16_R12); `iter` is the hop's index within the jobs' smearing call (it
+// reads scale slot iter and writes slot iter + 1 of each job's record).
+constexpr int kMaxF16Jobs = 64;
+struct F16HopJob {
+  const void* in;
+  void* out;
+  const void* U;
+  float kappa;
+  ScaleRecord* rec;
+};
+bool f16_hop_supported(const Geom& g);
+int launch_hop_f16(const F16HopJob* jobs, int njobs, int lprec, const Geom& g, int iter, cudaStream_t s);
+// Scale slots of a smearing call: slot 0 = the field's scale, slots 1..n
+// cleared (init); the field's scale = slot n (final).
+int f16_scale_init(ScaleRecord* const* recs, const int* n_iter, int njobs, cudaStream_t s);
+int f16_scale_final(ScaleRecord* const* recs, const int* n_iter, int njobs, cudaStream_t s);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

@@ -132,6 +132,43 @@ bool same_lattice(const Geom& a, const Geom& b) {
   return a.jd == b.jd;
 }
 
+// Float16 propagators: tensor-core hops with the per-iteration scale slots
+// of psi's scale record (slot 0 = psi's scale, slot n = the result's).
+int gauss_smear_f16(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay, qdpg_field_t scratch,
+                    cudaStream_t s) {
+  const Geom& g = psi->g;
+  if (j_decay != g.jd)
+    return fail(QDPG_ERR_UNSUPPORTED, "gauss_smear (f16): j_decay must be the lattice's decay direction");
+  if (n_iter > QDPG_F16_MAX_ITER)
+    return fail(QDPG_ERR_ARG, "gauss_smear (f16): at most %d iterations per call", QDPG_F16_MAX_ITER);
+  if (!f16_hop_supported(g))
+    return fail(QDPG_ERR_UNSUPPORTED,
+                "gauss_smear (f16): lattice not served (first spatial extent must be a multiple of 4, at most 64)");
+  const size_t bytes = f16_data_bytes(g.V);
+  void* tmp = scratch ? scratch->data : nullptr;
+  bool owned = false;
+  if (!tmp) {
+    cudaError_t e = cudaMallocAsync(&tmp, bytes, s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_NOMEM, "gauss_smear: scratch allocation of %zu bytes: %s", bytes,
+                                      cudaGetErrorString(e));
+    owned = true;
+  }
+  ScaleRecord* rec = psi->rec;
+  int rc = f16_scale_init(&rec, &n_iter, 1, s);
+  void* bufs[2] = {psi->data, tmp};
+  for (int it = 0; it < n_iter && rc == QDPG_OK; ++it) {
+    const F16HopJob job{bufs[it & 1], bufs[(it + 1) & 1], U->data, (float)kappa, rec};
+    rc = launch_hop_f16(&job, 1, U->prec, g, it, s);
+  }
+  if (rc == QDPG_OK) rc = f16_scale_final(&rec, &n_iter, 1, s);
+  if (rc == QDPG_OK && (n_iter & 1)) {
+    cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "gauss_smear: copy-back: %s", cudaGetErrorString(e));
+  }
+  if (owned) cudaFreeAsync(tmp, s);
+  return rc;
+}
+
 }  // namespace
 
 // One hop psi -> out with whichever kernel serves the geometry (see launch_hop).
@@ -155,9 +192,11 @@ int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter,
   if (U->kind != QDPG_GAUGE) return fail(QDPG_ERR_SHAPE, "gauss_smear: U must be a gauge field");
   if (psi->kind != QDPG_PROPAGATOR && psi->kind != QDPG_FERMION)
     return fail(QDPG_ERR_SHAPE, "gauss_smear: psi must be a propagator or fermion");
-  if (psi->prec != QDPG_F32 && psi->prec != QDPG_BF16)
-    return fail(QDPG_ERR_DTYPE, "gauss_smear: psi storage must be F32 or BF16");
+  if (psi->prec != QDPG_F32 && psi->prec != QDPG_BF16 && psi->prec != QDPG_F16)
+    return fail(QDPG_ERR_DTYPE, "gauss_smear: psi storage must be F32, BF16 or F16");
   if (!same_lattice(U->g, psi->g)) return fail(QDPG_ERR_SHAPE, "gauss_smear: U and psi on different lattices");
+  if ((psi->prec == QDPG_F16) != is_f16(U->prec))
+    return fail(QDPG_ERR_DTYPE, "gauss_smear: F16 propagators go with F16/F16_R12 links and only with them");
   if (j_decay < 0 || j_decay > 3) return fail(QDPG_ERR_ARG, "gauss_smear: j_decay %d outside 0..3", j_decay);
   if (n_iter < 0) return fail(QDPG_ERR_ARG, "gauss_smear: negative iteration count");
   if (!(kappa == kappa) || kappa > 1e30 || kappa < -1e30) return fail(QDPG_ERR_ARG, "gauss_smear: kappa not finite");
@@ -167,6 +206,7 @@ int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter,
     if (scratch->data == psi->data) return fail(QDPG_ERR_ARG, "gauss_smear: scratch aliases psi");
   }
   if (n_iter == 0) return ok();
+  if (psi->prec == QDPG_F16) return gauss_smear_f16(U, psi, kappa, n_iter, j_decay, scratch, as_stream(stream));
 
   cudaStream_t s = as_stream(stream);
   const size_t bytes = (size_t)psi->g.V * psi->ncomp * psi->esize;

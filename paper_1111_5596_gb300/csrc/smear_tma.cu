@@ -115,6 +115,7 @@ TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
 int launch_hop_tma_cfg(const tma_smear::JobPtrs* jobs, int njobs, int lprec, int psi_prec, const Geom& g,
                        cudaStream_t s, const TileCfg& cfg) {
   if (njobs < 1 || njobs > tma_smear::kMaxJobs) return QDPG_ERR_UNSUPPORTED;
+  if ((psi_prec != QDPG_F32 && psi_prec != QDPG_BF16) || is_f16(lprec)) return QDPG_ERR_UNSUPPORTED;
   const bool bf = psi_prec == QDPG_BF16;
   tma_smear::HopLaunch a;
   const bool lr12 = lprec == QDPG_F32_R12 || lprec == QDPG_BF16_R12;
@@ -174,6 +175,8 @@ int qdpg_tune_smear(qdpg_field_t U, qdpg_field_t psi, qdpg_field_t scratch, int 
       scratch->prec != psi->prec || scratch->data == psi->data)
     return fail(QDPG_ERR_SHAPE, "tune_smear: needs a gauge field, a propagator and a distinct scratch propagator");
   if (reps < 1 || reps > 1000) return fail(QDPG_ERR_ARG, "tune_smear: reps outside 1..1000");
+  if ((psi->prec != QDPG_F32 && psi->prec != QDPG_BF16) || is_f16(U->prec))
+    return fail(QDPG_ERR_UNSUPPORTED, "tune_smear: only the F32/BF16 pipelined kernel has tunable launch shapes");
   const Geom& g = psi->g;
   int hop_mu[3], k = 0;
   for (int mu = 0; mu < 4; ++mu)

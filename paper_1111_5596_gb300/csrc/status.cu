@@ -19,6 +19,7 @@ bool g_force_simple = false;
 int g_tile_consumers = 0;  // 0: the library's default for the geometry
 int g_tile_stages = 0;
 int g_tile_grid = 0;
+int g_f16_warps = 0;  // 0: the library's default (16)
 
 }  // namespace
 
@@ -40,6 +41,7 @@ bool debug_force_simple_hop() { return g_force_simple; }
 int debug_tile_consumers() { return g_tile_consumers; }
 int debug_tile_stages() { return g_tile_stages; }
 int debug_tile_grid() { return g_tile_grid; }
+int debug_f16_warps() { return g_f16_warps; }
 
 }  // namespace qdpg
 
@@ -86,6 +88,10 @@ int qdpg_debug_set(int what, long long value) {
     case QDPG_TUNE_STAGES:
       if (value != 0 && (value < 2 || value > 16)) return fail(QDPG_ERR_ARG, "debug_set: stages outside 2..16");
       g_tile_stages = (int)value;
+      return ok();
+    case QDPG_TUNE_F16_WARPS:
+      if (value != 0 && value != 8 && value != 16) return fail(QDPG_ERR_ARG, "debug_set: f16 consumer warps must be 8 or 16");
+      g_f16_warps = (int)value;
       return ok();
     case QDPG_TUNE_GRID:
       if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: grid mode outside 0..1");

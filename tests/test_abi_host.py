@@ -9,7 +9,7 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 HEADER = os.path.join(ROOT, "include", "qdpg.h")
 
-OK, ERR_ARG, ERR_SHAPE, ERR_DTYPE = 0, -1, -2, -3
+OK, ERR_ARG, ERR_SHAPE, ERR_DTYPE, ERR_UNSUPPORTED = 0, -1, -2, -3, -7
 
 
 @pytest.fixture(scope="module")
@@ -70,6 +70,13 @@ def test_field_bytes_and_wrap_validation(q):
     assert fb(lat, q.GAUGE, q.BF16_R12) == V * 24 * 4
     assert fb(lat, q.FERMION, q.F32) == V * 12 * 8
     assert fb(lat, q.PROPAGATOR, q.F32_R12) == 0               # reconstruct-12 is gauge-only
+    # float16 propagators: site-major data, padded to 256 bytes, then the scale record
+    assert fb(lat, q.PROPAGATOR, q.F16) == (V * 144 * 4 + 255) // 256 * 256 + q.F16_RECORD_BYTES
+    assert fb(lat, q.GAUGE, q.F16) == V * 36 * 4
+    assert fb(lat, q.GAUGE, q.F16_R12) == V * 24 * 4
+    assert fb(lat, q.FERMION, q.F16) == 0                        # float16 is propagator/gauge only
+    assert fb(lat, q.PROPAGATOR, q.F16_R12) == 0
+    assert fb(lat, q.PROPAGATOR, 6) == 0
     h = ctypes.c_void_p()
     fake = ctypes.c_void_p(1 << 20)                             # never dereferenced by wrap
     need = fb(lat, q.FERMION, q.F32)
@@ -154,6 +161,21 @@ def test_operation_argument_errors_are_caught_on_host(q):
     assert b(P, P, 1, 1, mom, 65, None, out, None) == ERR_ARG
     assert L.qdpg_field_import(P, None, 0, None) == ERR_ARG
     assert L.qdpg_field_import(P, out, 7, None) == ERR_DTYPE
+    # float16 propagators go with float16 links, on the layout's decay direction
+    PH = _wrap(q, lat, q.PROPAGATOR, q.F16, 1 << 35)
+    PH2 = _wrap(q, lat, q.PROPAGATOR, q.F16, 1 << 36)
+    UH = _wrap(q, lat, q.GAUGE, q.F16_R12, 1 << 37)
+    assert gs(U, PH, 0.2, 2, 3, None, None) == ERR_DTYPE
+    assert gs(UH, P, 0.2, 2, 3, None, None) == ERR_DTYPE
+    assert gs(UH, PH, 0.2, 2, 1, None, None) == ERR_UNSUPPORTED
+    assert gs(UH, PH, 0.2, 1000, 3, None, None) == ERR_ARG       # more iterations than scale slots
+    assert gs(UH, PH, 0.2, 2, 3, P, None) == ERR_SHAPE           # scratch precision
+    assert gs(UH, PH, 0.2, 2, 3, PH, None) == ERR_ARG            # scratch aliases psi
+    assert L.qdpg_gauss_smear_noalloc(UH, PH, 0.2, 2, 3, None) == ERR_DTYPE
+    assert m(PH, P, g, g, 1, mom, 1, None, out, None) == ERR_DTYPE
+    assert b(PH, P, 0, 1, mom, 1, None, out, None) == ERR_DTYPE
+    assert sh(PH, P, 1, 0, None) == ERR_SHAPE
+    assert L.qdpg_tune_smear(UH, PH, PH2, 3, 2, None) == ERR_UNSUPPORTED
     assert q.launch_count() == launches_before                    # every error came before a launch
 
 
