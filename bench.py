@@ -243,12 +243,15 @@ def traffic_for(kernel: str):
 
 
 def batch_arms(q, dev, args) -> dict:
-    """The 64 uneven smearing + meson jobs three ways on the same inputs:
+    """The 64 uneven smearing + meson jobs four ways on the same inputs:
     FP32 one job at a time (gauss_smear + meson_2pt per job), FP32 as one
-    batch replayed from a CUDA graph, and BF16 storage with BF16
-    reconstruct-12 links as one batch from a graph.  Each pass re-imports
-    every propagator, smears it with its own (kappa, N) and contracts the 16
-    zero-momentum mesons.  Returns times, throughput and the BF16 error."""
+    batch replayed from a CUDA graph, BF16 storage with BF16 reconstruct-12
+    links as one batch from a graph, and float16 storage (per-field
+    power-of-two scale) with float16 reconstruct-12 links on the tensor-core
+    hop as one batch from a graph.  Each pass re-imports every propagator,
+    smears it with its own (kappa, N) and contracts the 16 zero-momentum
+    mesons.  Returns times, throughput and the reduced-precision errors
+    against the FP32 results (which agree with the FP64 checker to 1e-5)."""
     import torch
 
     from synth import configs, device as synth_dev
@@ -265,14 +268,15 @@ def batch_arms(q, dev, args) -> dict:
         P_can = synth_dev.propagator(dims, j["seed"], dev)
         r = {"job": j, "lat": lat, "P": P_can,
              "U32": q.Field(lat, q.GAUGE, q.F32, device=dev).import_(U_can),
-             "Ub": q.Field(lat, q.GAUGE, q.BF16_R12, device=dev).import_(U_can)}
+             "Ub": q.Field(lat, q.GAUGE, q.BF16_R12, device=dev).import_(U_can),
+             "Uh": q.Field(lat, q.GAUGE, q.F16_R12, device=dev).import_(U_can)}
         del U_can
-        for tag, prec in (("32", q.F32), ("b", q.BF16)):
+        for tag, prec in (("32", q.F32), ("b", q.BF16), ("h", q.F16)):
             r["p" + tag] = q.Field(lat, q.PROPAGATOR, prec, device=dev)
             r["s" + tag] = r["p" + tag].like()
         r["m1"] = torch.zeros((16, 1, lat.Nt), dtype=torch.complex128, device=dev)
-        r["m32"] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
-        r["mb"] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
+        for tag in ("32", "b", "h"):
+            r["m" + tag] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
         rows.append(r)
     # launch shapes per (lattice, precision) class, by the autotuner
     if not args.no_tune:
@@ -285,6 +289,7 @@ def batch_arms(q, dev, args) -> dict:
                     q.tune_smear(U, r["p" + tag].import_(r["P"]), r["s" + tag], 3, reps=2)
     b32 = q.Batch([(r["U32"], r["p32"], r["s32"], r["job"]["kappa"], r["job"]["n_iter"], r["m32"]) for r in rows])
     bb = q.Batch([(r["Ub"], r["pb"], r["sb"], r["job"]["kappa"], r["job"]["n_iter"], r["mb"]) for r in rows])
+    bh = q.Batch([(r["Uh"], r["ph"], r["sh"], r["job"]["kappa"], r["job"]["n_iter"], r["mh"]) for r in rows])
 
     def single_fp32():
         for r in rows:
@@ -314,6 +319,7 @@ def batch_arms(q, dev, args) -> dict:
     t_single = timed(single_fp32)
     t_b32 = timed(lambda: batched(b32, "32"))
     t_bb = timed(lambda: batched(bb, "b"))
+    t_bh = timed(lambda: batched(bh, "h"))
 
     # correlator error of the BF16 batch against FP32, per job: max over
     # channels of ||C_bf16(.) - C_f32(.)|| / ||C_f32(.)|| over t
@@ -324,6 +330,7 @@ def batch_arms(q, dev, args) -> dict:
         return float((d / n).max())
 
     errs = [corr_err(r["mb"], r["m32"]) for r in rows]
+    errs_h = [corr_err(r["mh"], r["m32"]) for r in rows]
     # FP32 one at a time and FP32 batched run the same per-site arithmetic:
     # the smeared fields agree bit for bit (the correlators only to the
     # order of their FP64 atomic timeslice sums)
@@ -339,10 +346,11 @@ def batch_arms(q, dev, args) -> dict:
     same = all(torch.equal(f, r["p32"].storage) for f, r in zip(single_fields, rows))
     del single_fields
     mes_dev = max(corr_err(r["m1"][:, 0, :], r["m32"]) for r in rows)
-    by_n = {}
-    for r, e in zip(rows, errs):
+    by_n, by_n_h = {}, {}
+    for r, e, eh in zip(rows, errs, errs_h):
         band = "N<=25" if r["job"]["n_iter"] <= 25 else "N>25"
         by_n[band] = max(by_n.get(band, 0.0), e)
+        by_n_h[band] = max(by_n_h.get(band, 0.0), eh)
     hop_sites = sum(r["job"]["n_iter"] * r["lat"].V for r in rows)
     sites = sum(r["lat"].V for r in rows)
     # FP32-equivalent algorithmic bytes of a pass: import, N hops, mesons
@@ -351,13 +359,21 @@ def batch_arms(q, dev, args) -> dict:
         "workload": w.name, "jobs": len(rows),
         "lattices": {f"{d[0]}^3x{d[3]}": sum(1 for r in rows if r["job"]["dims"] == d) for d in lats},
         "hop_sites_per_pass": hop_sites, "contraction_sites_per_pass": sites,
-        "ms_per_pass": {"fp32_single": t_single, "fp32_batched_graph": t_b32, "bf16_batched_graph": t_bb},
+        "ms_per_pass": {"fp32_single": t_single, "fp32_batched_graph": t_b32, "bf16_batched_graph": t_bb,
+                        "f16_tc_batched_graph": t_bh},
         "fp32_equiv_gbs": {"fp32_single": bytes32 / t_single / 1e6, "fp32_batched_graph": bytes32 / t_b32 / 1e6,
-                           "bf16_batched_graph": bytes32 / t_bb / 1e6},
+                           "bf16_batched_graph": bytes32 / t_bb / 1e6, "f16_tc_batched_graph": bytes32 / t_bh / 1e6},
+        "speedup_f16_tc_batched_vs_fp32_single": t_single / t_bh,
+        "f16_vs_fp32_corr_rel_err_max": max(errs_h), "f16_vs_fp32_corr_rel_err_max_by_n": by_n_h,
+        "f16_tol": 2e-2, "f16_within_tol": max(errs_h) <= 2e-2,
+        "f16_storage": "propagators float16 x per-field power-of-two scale, links float16 reconstruct-12, "
+                       "tensor-core hop (mma.sync m16n8k16, FP32 accumulation)",
         "speedup_bf16_batched_vs_fp32_single": t_single / t_bb,
         "speedup_fp32_batched_vs_fp32_single": t_single / t_b32,
         "bf16_vs_fp32_corr_rel_err_max": max(errs), "bf16_vs_fp32_corr_rel_err_max_by_n": by_n,
         "bf16_tol": 2e-2, "bf16_within_tol": max(errs) <= 2e-2,
+        "f16_jobs_err": sorted([[r["job"]["dims"][0], r["job"]["n_iter"], round(e, 5)] for r, e in zip(rows, errs_h)],
+                               key=lambda x: x[1]),
         "bf16_jobs_err": sorted([[r["job"]["dims"][0], r["job"]["n_iter"], round(e, 5)] for r, e in zip(rows, errs)],
                                 key=lambda x: x[1]),
         "fp32_batched_fields_equal_single_bitwise": bool(same),

@@ -8,7 +8,10 @@
 // items of all those jobs share one persistent grid); jobs drop out as their
 // own count is reached.  After the last step, jobs with an odd count copy
 // their result back from the scratch buffer and the sixteen meson
-// correlators at zero momentum are contracted per job.  qdpg_batch_run can
+// correlators at zero momentum are contracted per job.  Float16 jobs use
+// the tensor-core hop and carry their per-iteration scale slots (set up
+// before the first step, folded into each field's scale after the last).
+// qdpg_batch_run can
 // replay the whole sequence as one CUDA graph: the first run executes the
 // launches directly (which also performs every lazy set-up) and captures
 // them; later runs launch the graph.
@@ -67,8 +70,38 @@ int issue(qdpg_batch* b, cudaStream_t s) {
   std::vector<const void*> in, U;
   std::vector<void*> out;
   std::vector<float> kap;
+  // float16 jobs: their scale slots (slot 0 = the field's scale)
+  std::vector<ScaleRecord*> recs;
+  std::vector<int> niters;
+  for (const Job& J : b->jobs)
+    if (J.psi.prec == QDPG_F16 && J.n_iter > 0) {
+      recs.push_back(J.psi.rec);
+      niters.push_back(J.n_iter);
+    }
+  for (size_t off = 0; off < recs.size(); off += kMaxF16Jobs) {
+    const int n = (int)std::min<size_t>(kMaxF16Jobs, recs.size() - off);
+    int rc = f16_scale_init(recs.data() + off, niters.data() + off, n, s);
+    if (rc != QDPG_OK) return rc;
+  }
+  std::vector<F16HopJob> hjobs;
   for (int it = 0; it < b->max_iter; ++it) {
     for (const JobClass& c : b->classes) {
+      if (b->jobs[c.jobs[0]].psi.prec == QDPG_F16) {
+        hjobs.clear();
+        for (int j : c.jobs) {
+          const Job& J = b->jobs[j];
+          if (J.n_iter <= it) continue;
+          void* bufs[2] = {J.psi.data, J.scratch.data};
+          hjobs.push_back(F16HopJob{bufs[it & 1], bufs[(it + 1) & 1], J.U.data, J.kappa, J.psi.rec});
+        }
+        const Job& J0 = b->jobs[c.jobs[0]];
+        for (size_t off = 0; off < hjobs.size(); off += kMaxF16Jobs) {
+          const int n = (int)std::min<size_t>(kMaxF16Jobs, hjobs.size() - off);
+          int rc = launch_hop_f16(hjobs.data() + off, n, J0.U.prec, J0.psi.g, it, s);
+          if (rc != QDPG_OK) return rc;
+        }
+        continue;
+      }
       in.clear();
       out.clear();
       U.clear();
@@ -102,6 +135,11 @@ int issue(qdpg_batch* b, cudaStream_t s) {
         }
       }
     }
+  }
+  for (size_t off = 0; off < recs.size(); off += kMaxF16Jobs) {
+    const int n = (int)std::min<size_t>(kMaxF16Jobs, recs.size() - off);
+    int rc = f16_scale_final(recs.data() + off, niters.data() + off, n, s);
+    if (rc != QDPG_OK) return rc;
   }
   static const int chans[16] = {0, 1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14, 15};
   static const int zero[3] = {0, 0, 0};
@@ -147,9 +185,18 @@ int qdpg_batch_create(const qdpg_job* jobs, int njobs, int j_decay, qdpg_batch_t
     if (q.U->kind != QDPG_GAUGE || (q.psi->kind != QDPG_PROPAGATOR && q.psi->kind != QDPG_FERMION) ||
         q.scratch->kind != q.psi->kind || q.scratch->prec != q.psi->prec || q.scratch->data == q.psi->data ||
         !same_geom(q.U->g, q.psi->g) || !same_geom(q.scratch->g, q.psi->g) ||
-        (q.psi->prec != QDPG_F32 && q.psi->prec != QDPG_BF16)) {
+        (q.psi->prec != QDPG_F32 && q.psi->prec != QDPG_BF16 && q.psi->prec != QDPG_F16)) {
       delete b;
       return fail(QDPG_ERR_SHAPE, "batch_create: job %d: fields do not match (gauge, psi, distinct scratch)", i);
+    }
+    if ((q.psi->prec == QDPG_F16) != is_f16(q.U->prec)) {
+      delete b;
+      return fail(QDPG_ERR_DTYPE, "batch_create: job %d: F16 propagators go with F16/F16_R12 links only", i);
+    }
+    if (q.psi->prec == QDPG_F16 && (j_decay != q.psi->g.jd || q.n_iter > QDPG_F16_MAX_ITER)) {
+      delete b;
+      return fail(QDPG_ERR_UNSUPPORTED, "batch_create: job %d: F16 smearing needs the lattice's decay direction "
+                                        "and at most %d iterations", i, QDPG_F16_MAX_ITER);
     }
     if (q.n_iter < 0 || !(q.kappa == q.kappa)) {
       delete b;

@@ -1,10 +1,11 @@
 """Batched smearing + mesons (many sources at once, Sec. 5) against the FP64
 checker and against the one-job entry points, through the C ABI.
 
-The batch mixes two lattices, FP32 and BF16 storage, propagators and a
-fermion, and iteration counts 0..8 (even and odd), so that jobs leave the
-multi-job launches at different steps and both the multi-job pipelined
-kernel and the per-job fallback run.
+The batch mixes three lattices, FP32, BF16 and float16 storage,
+propagators and a fermion, and iteration counts 0..9 (even and odd), so
+that jobs leave the multi-job launches at different steps and the
+multi-job pipelined kernel, the multi-job tensor-core kernel and the
+per-job fallback all run.
 """
 import numpy as np
 import pytest
@@ -27,6 +28,9 @@ JOBS = [
     ((6, 4, 8, 3), "prop", "f32", "f32", 0.20, 4, True),    # lattice of its own class
     ((8, 8, 8, 4), "prop", "bf16", "bf16_r12", 0.21, 7, True),
     ((8, 8, 8, 4), "ferm", "f32", "f32", 0.22, 6, False),   # one vector: per-job kernel
+    ((8, 8, 8, 4), "prop", "f16", "f16_r12", 0.27, 9, True),  # float16: tensor-core multi-job hop
+    ((8, 8, 8, 4), "prop", "f16", "f16_r12", 0.19, 4, True),
+    ((12, 12, 4, 2), "prop", "f16", "f16", 0.22, 6, True),
 ]
 
 
