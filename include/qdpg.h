@@ -129,7 +129,8 @@ int qdpg_last_error(char* buf, size_t n);
 /* ---- kernel timing ------------------------------------------------------
  * When enabled, each kernel the library launches is bracketed by two CUDA
  * events recorded on its own stream.  Kernel names: "smear_hop",
- * "meson_2pt", "field_import", "field_export", "shift", "point_source".
+ * "smear_hop_f16", "meson_2pt", "baryon_2pt", "momentum_project", "field_import",
+ * "field_export", "shift", "point_source".
  * query() waits for the recorded events and returns the summed elapsed time
  * (ms) and launch count for one name since the last reset().  At most 65536
  * launches are recorded per window.  Host-side bookkeeping is thread-safe. */
@@ -211,25 +212,30 @@ void qdpg_field_release(qdpg_field_t f);
 /* Convert a canonical-layout buffer (device memory, element type `canon`)
  * into `dst`'s device layout and precision.  F32 storage rounds to nearest
  * even; BF16 rounds to nearest even from the value given; reconstruct-12
- * keeps rows 0 and 1.  The source must hold V*ncomp complex numbers
- * (gauge: 4*V*9). */
+ * keeps rows 0 and 1.  F16 propagators first find the largest |re|, |im|
+ * (M), set exp = e - 14 where M = f 2^e with f in [0.5, 1), and store the
+ * values times 2^-exp rounded to nearest even (two kernels); F16 links are
+ * rounded directly.  The source must hold V*ncomp complex numbers (gauge:
+ * 4*V*9). */
 int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* stream);
 
 /* Write `src` to a canonical complex-double buffer in device memory
- * (reconstruct-12 gauge fields are expanded to all nine entries). */
+ * (reconstruct-12 gauge fields are expanded to all nine entries; F16
+ * propagators are multiplied by 2^exp, which is exact). */
 int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream);
 
 /* Point source at x0 (Sec. 5 "source creation"): zero the field, then set
  * the unit entries at x0.  PROPAGATOR: all twelve columns,
  * S[s c][s' c'] = delta_ss' delta_cc'; FERMION: the single entry
- * spin_color = s*3 + c (0..11).  F32 or BF16 storage. */
+ * spin_color = s*3 + c (0..11).  F32, BF16 or (propagators) F16 storage;
+ * an F16 propagator's scale becomes exp = 0. */
 int qdpg_point_source(qdpg_field_t f, const int x0[4], int spin_color, void* stream);
 
 /* ---- shift (QDP++ nearest-neighbour access, Sec. 1) ---------------------- */
 
 /* dst(x) = src(x + sign*mu_hat), periodic; sign = +1 (FORWARD) or -1.
  * dst and src must be distinct fields of the same kind, precision and
- * lattice.  Bit-exact copy of elements. */
+ * lattice.  Bit-exact copy of elements (and of an F16 propagator's scale). */
 int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* stream);
 
 /* ---- Gaussian smearing (Sec. 5: SRC and SNK stages) --------------------- */
@@ -239,8 +245,15 @@ int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* strea
  *                                                  + U_i(x-i)^dag psi(x-i) ]
  * acting on colour; every spin and source column is smeared alike.
  * U: QDPG_GAUGE (F32, F32_R12, BF16_R12 or BF16); psi: FERMION or
- * PROPAGATOR (F32 or BF16), same lattice.  Arithmetic is FP32 for every
- * storage precision.  j_decay selects the direction that is NOT smeared.
+ * PROPAGATOR (F32 or BF16), same lattice.  Or: psi an F16 PROPAGATOR with
+ * U in F16 or F16_R12 (and only then F16 links), smeared by the tensor-core
+ * kernel (float16 products, FP32 sums); it needs j_decay equal to the
+ * lattice's decay direction, the first non-decay extent a multiple of 4 and
+ * at most 64 (QDPG_ERR_UNSUPPORTED otherwise) and n_iter <=
+ * QDPG_F16_MAX_ITER; each iteration rescales the stored numbers by a power
+ * of two chosen from the previous iteration's largest magnitude, using the
+ * scale slots of psi's record.  Arithmetic is FP32 for every storage
+ * precision.  j_decay selects the direction that is NOT smeared.
  * scratch: a field of psi's kind/precision/lattice used as the ping-pong
  * buffer; if NULL the library allocates one stream-ordered
  * (cudaMallocAsync) and frees it after the last iteration.  n_iter = 0 is a
@@ -276,8 +289,9 @@ int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double kappa, int
  * Gamma(n) = g1^n0 g2^n1 g3^n2 g4^n3 in the DeGrand-Rossi basis (n in 0..15,
  * Gamma(15) = gamma_5), p_k = 2 pi (moms[3k]/L_a, moms[3k+1]/L_b,
  * moms[3k+2]/L_c) over the three non-decay directions a < b < c.
- * S1, S2: PROPAGATOR fields (F32 or BF16) on the same lattice (may be the
- * same field).  origin: 4 ints or NULL (= 0).
+ * S1, S2: PROPAGATOR fields (F32, BF16 or F16, both the same) on the same
+ * lattice (may be the same field); F16 sums are multiplied by
+ * 2^(exp1 + exp2).  origin: 4 ints or NULL (= 0).
  * out_dev: device buffer of n_chan*n_mom*Nt complex doubles (2 doubles,
  * re then im), overwritten.  Site products are FP32; timeslice and momentum
  * sums are FP64.  Limits: n_chan <= 256, n_mom <= 64. */
@@ -296,7 +310,8 @@ int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const
  * chibar = eps_a'b'c' ubar_c' (qbar_b' Gbar qbar_a'^T), Gbar = g4 G^dag g4
  * (DeGrand-Rossi basis).  Every Wick pairing enters with the sign of the
  * Grassmann reordering; the fully nested pairing has sign +1.  Su, Sd:
- * point-to-all PROPAGATOR fields (F32 or BF16, same lattice); Sd is used by
+ * point-to-all PROPAGATOR fields (F32, BF16 or F16, both the same, same
+ * lattice; F16 sums are multiplied by 2^(2 exp_u + exp_d)); Sd is used by
  * the nucleon only and may be NULL for the Delta.  origin: 4 ints or NULL;
  * momenta as in qdpg_meson_2pt.  out_dev: device buffer of n_mom*Nt
  * complex doubles, overwritten.  Site values FP32, sums FP64.
@@ -309,7 +324,8 @@ int qdpg_baryon_2pt(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, cons
 /* Site values instead of sums: sites_dev (device, 8-byte aligned) receives
  * complex floats sites[j][t][x3] = the channel-j site trace of
  * qdpg_meson_2pt at the site (t, x3) (device layout order), n_chan*Nt*V3
- * of them. */
+ * of them (F16 fields: scaled by the power of two in FP32, which can
+ * overflow for fields smeared far beyond 2^60). */
 int qdpg_meson_sites(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
                      void* sites_dev, void* stream);
 
@@ -340,7 +356,7 @@ int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, int n_chan,
  * they point to are borrowed and must outlive the batch. */
 typedef struct {
   qdpg_field_t U;       /* QDPG_GAUGE, any link precision */
-  qdpg_field_t psi;     /* PROPAGATOR or FERMION, F32 or BF16 (mesons: PROPAGATOR) */
+  qdpg_field_t psi;     /* PROPAGATOR or FERMION, F32 or BF16; or PROPAGATOR F16 (with F16/F16_R12 links) */
   qdpg_field_t scratch; /* same kind/precision/lattice as psi, distinct buffer */
   double kappa;
   int n_iter;           /* >= 0; jobs of one batch may differ */
@@ -356,7 +372,11 @@ typedef struct qdpg_batch* qdpg_batch_t; /* opaque, owned by the library */
  * launch).  j_decay: the direction that is not smeared, as in
  * qdpg_gauss_smear.  Errors: QDPG_ERR_ARG for a null pointer, njobs or
  * j_decay out of range, negative n_iter or NaN kappa; QDPG_ERR_SHAPE for
- * fields that do not match.  Nothing is launched or allocated on the device. */
+ * fields that do not match; QDPG_ERR_DTYPE for F16 propagators without
+ * F16 links or the reverse; QDPG_ERR_UNSUPPORTED for F16 jobs whose
+ * j_decay is not the lattice's or whose n_iter exceeds QDPG_F16_MAX_ITER.
+ * Float16 jobs run on the tensor-core kernel with their own scale slots.
+ * Nothing is launched or allocated on the device. */
 int qdpg_batch_create(const qdpg_job* jobs, int njobs, int j_decay, qdpg_batch_t* out);
 
 /* Runs every job of the batch on `stream`.  use_graph = 0: the launches are
