@@ -49,15 +49,22 @@
  *
  *      ((t*3 + v/16) * V3 + s3) * 48 + (v%16)*3 + c
  *
- *  (three groups of 16 vectors, each group site-major).  The represented
- *  value is the stored pair times 2^exp, where exp is a per-field scale that
- *  keeps the stored numbers inside the float16 range while smearing grows
- *  the field by up to (1 + 6 kappa) per iteration.  exp and the largest
- *  stored magnitude live in a scale record of QDPG_F16_RECORD_BYTES bytes
- *  placed after the data, at byte offset round_up(V*144*4, 256); the record
- *  is part of the field (qdpg_field_bytes includes it) and every operation
- *  on the field reads or updates it on the device.  F16 gauge fields need
- *  no scale (|U_ab| <= 1) and use the component-major layout above.
+ *  (three groups of 16 vectors, each group site-major).
+ *
+ *  Scale record.  Every propagator and fermion field (any precision)
+ *  represents stored numbers times 2^exp, where exp is a per-field scale:
+ *  smearing grows a field by up to (1 + 6 kappa) per iteration, far beyond
+ *  the float16 range and, after squaring in the contractions, beyond FP32.
+ *  exp (and, for float16, the largest stored magnitude) lives in a scale
+ *  record of QDPG_SCALE_RECORD_BYTES bytes placed after the data, at byte
+ *  offset round_up(V*ncomp*esize, 256); the record is part of the field
+ *  (qdpg_field_bytes includes it) and every operation on the field reads or
+ *  updates it on the device.  Import and point source set exp = 0 (float16
+ *  import: the exponent that fits the data); export multiplies by 2^exp;
+ *  the contractions apply it to their FP64 sums.  Float16 propagators are
+ *  rescaled every iteration; FP32/BF16 fields only when the growth bound of
+ *  a smearing call, N log2(1 + 6|kappa|), exceeds 40 bits.  Gauge fields
+ *  need no scale (|U_ab| <= 1); F16 links use the component-major layout.
  *
  *  Canonical layout (import/export): complex numbers, site index
  *  x0 + L0*(x1 + L1*(x2 + L2*x3)); propagator/fermion/colour matrix are
@@ -104,10 +111,10 @@ typedef enum {
   QDPG_F16_R12 = 5    /* gauge only: float16 pair, two rows stored */
 } qdpg_prec;
 
-/* Size of the scale record of a QDPG_F16 propagator (see the layout notes):
- * int32 exp, float max |stored|, then the per-iteration scale slots of a
- * smearing call (at most QDPG_F16_MAX_ITER iterations per call). */
-#define QDPG_F16_RECORD_BYTES 8192
+/* Size of the scale record of a propagator or fermion (see the layout
+ * notes): int32 exp, float max |stored|, then the per-iteration scale slots
+ * of a float16 smearing call (at most QDPG_F16_MAX_ITER iterations). */
+#define QDPG_SCALE_RECORD_BYTES 8192
 #define QDPG_F16_MAX_ITER 999
 
 typedef enum {

@@ -22,7 +22,7 @@ LIB_PATH = os.path.join(HERE, "libqdpg.so")
 COLOR_MATRIX, GAUGE, FERMION, PROPAGATOR = 0, 1, 2, 3
 F32, BF16, F32_R12, BF16_R12, F16, F16_R12 = 0, 1, 2, 3, 4, 5
 CANON_F64, CANON_F32 = 0, 1
-F16_RECORD_BYTES = 8192
+SCALE_RECORD_BYTES = 8192
 
 PREC_NAMES = {"f32": F32, "bf16": BF16, "f32_r12": F32_R12, "bf16_r12": BF16_R12, "f16": F16, "f16_r12": F16_R12}
 

@@ -116,7 +116,7 @@ size_t qdpg_field_bytes(qdpg_lattice_t lat, int kind, int prec) {
   if (!lat) return 0;
   int nc = ncomp_of(kind, prec);
   if (!nc) return 0;
-  if (kind == QDPG_PROPAGATOR && prec == QDPG_F16) return f16_data_bytes(lat->g.V) + QDPG_F16_RECORD_BYTES;
+  if (has_scale_record(kind)) return data_bytes_rounded(lat->g.V, nc, esize_of(prec)) + QDPG_SCALE_RECORD_BYTES;
   return (size_t)lat->g.V * (size_t)nc * (size_t)esize_of(prec);
 }
 
@@ -138,9 +138,9 @@ int qdpg_field_wrap(qdpg_lattice_t lat, int kind, int prec, void* dev_ptr, size_
   f->esize = esize_of(prec);
   f->data = dev_ptr;
   f->bytes = bytes;
-  f->rec = (kind == QDPG_PROPAGATOR && prec == QDPG_F16)
-               ? reinterpret_cast<ScaleRecord*>(static_cast<char*>(dev_ptr) + f16_data_bytes(lat->g.V))
-               : nullptr;
+  f->rec = has_scale_record(kind) ? reinterpret_cast<ScaleRecord*>(static_cast<char*>(dev_ptr) +
+                                                                    data_bytes_rounded(lat->g.V, nc, f->esize))
+                                   : nullptr;
   *out = f;
   return ok();
 }

@@ -134,6 +134,17 @@ int issue(qdpg_batch* b, cudaStream_t s) {
           if (rc != QDPG_OK) return rc;
         }
       }
+      // FP32/BF16 jobs whose growth bound needs it: exact power-of-two rescale
+      for (int j : c.jobs) {
+        const Job& J = b->jobs[j];
+        if (J.n_iter <= it) continue;
+        const RescalePlan plan = rescale_plan(J.kappa, J.n_iter);
+        if (plan.every && (it + 1) % plan.every == 0) {
+          void* latest = (it + 1) & 1 ? J.scratch.data : J.psi.data;
+          rc = launch_rescale(latest, J.psi.prec, J.psi.g.V * J.psi.ncomp, plan.shift, J.psi.rec, s);
+          if (rc != QDPG_OK) return rc;
+        }
+      }
     }
   }
   for (size_t off = 0; off < recs.size(); off += kMaxF16Jobs) {

@@ -81,7 +81,9 @@ __global__ void __launch_bounds__(kThreads) import_kernel(Dst* __restrict__ dst,
 // Thread per canonical complex entry; reconstructs row 2 of reconstruct-12 links.
 template <typename Dev>
 __global__ void __launch_bounds__(kThreads) export_kernel(double* __restrict__ out, const Dev* __restrict__ dev,
-                                                          Geom g, int kind, bool r12, int nc) {
+                                                          Geom g, int kind, bool r12, int nc,
+                                                          const ScaleRecord* rec) {
+  const int e2 = rec ? rec->exp : 0;  // value = stored * 2^exp
   const int nc_canon = (kind == QDPG_GAUGE) ? 9 : nc;
   const long long nmu = (kind == QDPG_GAUGE) ? 4 : 1;
   const long long total = nmu * g.V * nc_canon;
@@ -124,8 +126,8 @@ __global__ void __launch_bounds__(kThreads) export_kernel(double* __restrict__ o
       int comp = (kind == QDPG_GAUGE) ? mu * 9 + e : e;
       load_elem(base + (long long)comp * g.V3, re, im);
     }
-    out[2 * i] = re;
-    out[2 * i + 1] = im;
+    out[2 * i] = ldexp(re, e2);
+    out[2 * i + 1] = ldexp(im, e2);
   }
 }
 
@@ -348,7 +350,12 @@ int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* 
       import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
                                                      r12, dst->ncomp);
   }
-  return check_launch("field_import");
+  const int rc = check_launch("field_import");
+  if (rc == QDPG_OK && dst->rec) {  // imported values are unscaled: exp = 0
+    cudaError_t e = cudaMemsetAsync(dst->rec, 0, 2 * sizeof(int), s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "field_import: scale reset: %s", cudaGetErrorString(e));
+  }
+  return rc;
 }
 
 int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream) {
@@ -362,13 +369,13 @@ int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream) {
     f16_export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->rec);
   else if (is_f16(src->prec))
     export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->kind,
-                                            r12, src->ncomp);
+                                            r12, src->ncomp, src->rec);
   else if (is_bf16(src->prec))
     export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __nv_bfloat162*>(src->data), src->g,
-                                            src->kind, r12, src->ncomp);
+                                            src->kind, r12, src->ncomp, src->rec);
   else
     export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const float2*>(src->data), src->g, src->kind,
-                                            r12, src->ncomp);
+                                            r12, src->ncomp, src->rec);
   return check_launch("field_export");
 }
 
@@ -395,6 +402,7 @@ int qdpg_point_source(qdpg_field_t f, const int x0[4], int spin_color, void* str
   }
   size_t bytes = (size_t)g.V * f->ncomp * f->esize;
   cudaError_t e = cudaMemsetAsync(f->data, 0, bytes, s);
+  if (e == cudaSuccess && f->rec) e = cudaMemsetAsync(f->rec, 0, 2 * sizeof(int), s);  // exp = 0
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "point_source: memset: %s", cudaGetErrorString(e));
   const int t = x0[g.jd];
   const int s3 = x0[g.sd[0]] + g.sL[0] * (x0[g.sd[1]] + g.sL[1] * x0[g.sd[2]]);
@@ -430,7 +438,12 @@ int qdpg_shift(qdpg_field_t dst, qdpg_field_t src, int sign, int mu, void* strea
   else
     shift_kernel<<<grid, kThreads, 0, s>>>(static_cast<uint32_t*>(dst->data),
                                            static_cast<const uint32_t*>(src->data), src->g, src->ncomp, mu, sign);
-  return check_launch("shift");
+  const int rc = check_launch("shift");
+  if (rc == QDPG_OK && dst->rec && !is_f16_prop(src)) {  // the float16 kernel copies its scale itself
+    cudaError_t e = cudaMemcpyAsync(dst->rec, src->rec, 2 * sizeof(int), cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "shift: scale copy: %s", cudaGetErrorString(e));
+  }
+  return rc;
 }
 
 }  // extern "C"

@@ -32,9 +32,10 @@ struct qdpg_lattice {
 
 namespace qdpg {
 
-// Scale record of a QDPG_F16 propagator (device memory, after the data).
-// The field's value is stored * 2^exp.  cmax/cexp are the per-iteration
-// slots of one smearing call: hop k reads slot k and writes slot k+1.
+// Scale record of a propagator or fermion (device memory, after the data).
+// The field's value is stored * 2^exp.  For float16 propagators maxabs and
+// the per-iteration slots cmax/cexp of one smearing call (hop k reads slot k
+// and writes slot k+1) drive the rescaling; FP32/BF16 fields use exp only.
 constexpr int kScaleSlots = QDPG_F16_MAX_ITER + 1;
 struct ScaleRecord {
   int exp;            // value = stored * 2^exp
@@ -44,7 +45,7 @@ struct ScaleRecord {
   float cmax[kScaleSlots];
   int cexp[kScaleSlots];
 };
-static_assert(sizeof(ScaleRecord) <= QDPG_F16_RECORD_BYTES, "scale record too large");
+static_assert(sizeof(ScaleRecord) <= QDPG_SCALE_RECORD_BYTES, "scale record too large");
 
 // Word index of (t, comp, s3) in a QDPG_F16 propagator (see qdpg.h).
 __host__ __device__ inline long long f16_prop_index(int V3, int t, int comp, int s3) {
@@ -54,8 +55,13 @@ __host__ __device__ inline long long f16_prop_index(int V3, int t, int comp, int
   return ((long long)(t * 3 + (v >> 4)) * V3 + s3) * 48 + (v & 15) * 3 + c;
 }
 
-// Bytes of the data part of a field (the scale record follows, 256-aligned).
-inline size_t f16_data_bytes(long long V) { return (((size_t)V * 144 * 4) + 255) / 256 * 256; }
+// Propagators and fermions (every precision) carry a scale record after
+// their data, at the data size rounded up to 256 bytes.
+inline bool has_scale_record(int kind) { return kind == QDPG_PROPAGATOR || kind == QDPG_FERMION; }
+inline size_t data_bytes_rounded(long long V, int ncomp, int esize) {
+  return ((size_t)V * ncomp * esize + 255) / 256 * 256;
+}
+inline size_t f16_data_bytes(long long V) { return data_bytes_rounded(V, 144, 4); }
 
 }  // namespace qdpg
 
@@ -130,6 +136,16 @@ int launch_hop_f16(const F16HopJob* jobs, int njobs, int lprec, const Geom& g, i
 // cleared (init); the field's scale = slot n (final).
 int f16_scale_init(ScaleRecord* const* recs, const int* n_iter, int njobs, cudaStream_t s);
 int f16_scale_final(ScaleRecord* const* recs, const int* n_iter, int njobs, cudaStream_t s);
+
+// FP32/BF16 smearing whose growth bound N log2(1 + 6|kappa|) exceeds 40 bits
+// is rescaled by an exact power of two every `every` iterations (`shift`
+// bits down, added to the field's exp); every = 0: no rescaling.
+struct RescalePlan {
+  int every, shift;
+};
+RescalePlan rescale_plan(double kappa, int n_iter);
+// data *= 2^-shift elementwise (F32 or BF16 storage); rec->exp += shift.
+int launch_rescale(void* data, int prec, long long nelem, int shift, ScaleRecord* rec, cudaStream_t s);
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 

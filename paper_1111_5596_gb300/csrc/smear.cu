@@ -9,6 +9,8 @@
 // and reuses them for all colour vectors of the site, so link traffic is
 // paid once per site per iteration, not once per column.  Arithmetic is FP32
 // for every storage precision.
+#include <cmath>
+
 #include "qdpg_internal.h"
 #include "qdpg_profile.h"
 #include "smear_common.cuh"
@@ -126,6 +128,16 @@ int launch_hop(const void* in, void* out, const void* U, int lprec, const Geom& 
   return fail(QDPG_ERR_DTYPE, "gauss_smear: link precision %d", lprec);
 }
 
+// data *= 2^-shift (exact for normal numbers), one thread adds shift to exp.
+template <typename T>
+__global__ void __launch_bounds__(256) rescale_kernel(T* __restrict__ d, long long n, int shift, ScaleRecord* rec) {
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < n; i += (long long)gridDim.x * 256) {
+    const float2 v = ld2(d + i);
+    st2(d + i, make_float2(ldexpf(v.x, -shift), ldexpf(v.y, -shift)));
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rec->exp += shift;
+}
+
 bool same_lattice(const Geom& a, const Geom& b) {
   for (int mu = 0; mu < 4; ++mu)
     if (a.L[mu] != b.L[mu]) return false;
@@ -170,6 +182,29 @@ int gauss_smear_f16(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, 
 }
 
 }  // namespace
+
+RescalePlan rescale_plan(double kappa, int n_iter) {
+  const double g = std::log2(1.0 + 6.0 * std::fabs(kappa));  // growth bound, bits per iteration
+  RescalePlan p{0, 0};
+  if (!(g > 0.0) || n_iter * g <= 40.0) return p;
+  p.every = g >= 32.0 ? 1 : (int)std::floor(32.0 / g);
+  p.shift = (int)std::floor(p.every * g);
+  if (p.shift < 1) p.every = 0;
+  return p;
+}
+
+int launch_rescale(void* data, int prec, long long nelem, int shift, ScaleRecord* rec, cudaStream_t s) {
+  if (!rec) return fail(QDPG_ERR_ARG, "rescale: field has no scale record");
+  long long blocks = (nelem + 255) / 256;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (prec == QDPG_BF16)
+    rescale_kernel<<<(int)blocks, 256, 0, s>>>(static_cast<__nv_bfloat162*>(data), nelem, shift, rec);
+  else if (prec == QDPG_F32)
+    rescale_kernel<<<(int)blocks, 256, 0, s>>>(static_cast<float2*>(data), nelem, shift, rec);
+  else
+    return fail(QDPG_ERR_DTYPE, "rescale: precision %d", prec);
+  return check_launch("gauss_smear rescale");
+}
 
 // One hop psi -> out with whichever kernel serves the geometry (see launch_hop).
 int launch_hop_any(const void* in, void* out, const void* U, int lprec, int psi_prec, int cols, const Geom& g,
@@ -225,6 +260,7 @@ int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter,
   const int cols = psi->kind == QDPG_PROPAGATOR ? 12 : 1;
   void* bufs[2] = {psi->data, tmp};
   int rc = QDPG_OK;
+  const RescalePlan plan = rescale_plan((float)kappa, n_iter);  // the kernel's kappa
   for (int it = 0; it < n_iter && rc == QDPG_OK; ++it) {
     const void* in = bufs[it & 1];
     void* out = bufs[(it + 1) & 1];
@@ -232,6 +268,8 @@ int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter,
       rc = launch_hop<__nv_bfloat162>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
     else
       rc = launch_hop<float2>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
+    if (rc == QDPG_OK && plan.every && (it + 1) % plan.every == 0)
+      rc = launch_rescale(out, psi->prec, psi->g.V * psi->ncomp, plan.shift, psi->rec, s);
   }
   if (rc == QDPG_OK && (n_iter & 1)) {
     cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
@@ -318,6 +356,7 @@ extern "C" int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double
     if (mu != j_decay) hd.mu[k++] = mu;
   const int cols = psi->kind == QDPG_PROPAGATOR ? 12 : 1;
   void* bufs[2] = {psi->data, tmp};
+  const RescalePlan plan = rescale_plan((float)kappa, n_iter);  // the kernel's kappa
   for (int it = 0; it < n_iter && rc == QDPG_OK; ++it) {
     const void* in = bufs[it & 1];
     void* out = bufs[(it + 1) & 1];
@@ -325,6 +364,8 @@ extern "C" int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double
       rc = launch_hop<__nv_bfloat162>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
     else
       rc = launch_hop<float2>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
+    if (rc == QDPG_OK && plan.every && (it + 1) % plan.every == 0)
+      rc = launch_rescale(out, psi->prec, psi->g.V * psi->ncomp, plan.shift, psi->rec, s);
   }
   if (rc == QDPG_OK && (n_iter & 1)) {
     cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);

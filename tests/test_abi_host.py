@@ -63,15 +63,17 @@ def test_field_bytes_and_wrap_validation(q):
     rc, lat = _lat(q, (4, 6, 2, 3))
     V = 4 * 6 * 2 * 3
     fb = q._lib.qdpg_field_bytes
-    assert fb(lat, q.PROPAGATOR, q.F32) == V * 144 * 8
-    assert fb(lat, q.PROPAGATOR, q.BF16) == V * 144 * 4
+    rec = lambda n: (n + 255) // 256 * 256 + q.SCALE_RECORD_BYTES  # data padded to 256 B, then the scale record
+    assert fb(lat, q.PROPAGATOR, q.F32) == rec(V * 144 * 8)
+    assert fb(lat, q.PROPAGATOR, q.BF16) == rec(V * 144 * 4)
     assert fb(lat, q.GAUGE, q.F32) == V * 36 * 8
     assert fb(lat, q.GAUGE, q.F32_R12) == V * 24 * 8
     assert fb(lat, q.GAUGE, q.BF16_R12) == V * 24 * 4
-    assert fb(lat, q.FERMION, q.F32) == V * 12 * 8
+    assert fb(lat, q.FERMION, q.F32) == rec(V * 12 * 8)
+    assert fb(lat, q.COLOR_MATRIX, q.F32) == V * 9 * 8
     assert fb(lat, q.PROPAGATOR, q.F32_R12) == 0               # reconstruct-12 is gauge-only
     # float16 propagators: site-major data, padded to 256 bytes, then the scale record
-    assert fb(lat, q.PROPAGATOR, q.F16) == (V * 144 * 4 + 255) // 256 * 256 + q.F16_RECORD_BYTES
+    assert fb(lat, q.PROPAGATOR, q.F16) == rec(V * 144 * 4)
     assert fb(lat, q.GAUGE, q.F16) == V * 36 * 4
     assert fb(lat, q.GAUGE, q.F16_R12) == V * 24 * 4
     assert fb(lat, q.FERMION, q.F16) == 0                        # float16 is propagator/gauge only

@@ -28,6 +28,7 @@ JOBS = [
     ((6, 4, 8, 3), "prop", "f32", "f32", 0.20, 4, True),    # lattice of its own class
     ((8, 8, 8, 4), "prop", "bf16", "bf16_r12", 0.21, 7, True),
     ((8, 8, 8, 4), "ferm", "f32", "f32", 0.22, 6, False),   # one vector: per-job kernel
+    ((8, 8, 8, 4), "prop", "f32", "f32", 0.30, 45, True),   # growth 2^67: rescaled by 2^-31 twice
     ((8, 8, 8, 4), "prop", "f16", "f16_r12", 0.27, 9, True),  # float16: tensor-core multi-job hop
     ((8, 8, 8, 4), "prop", "f16", "f16_r12", 0.19, 4, True),
     ((12, 12, 4, 2), "prop", "f16", "f16", 0.22, 6, True),

@@ -289,3 +289,34 @@ def test_mesons_16x32_full_size_sampled_timeslices(qdpg_gpu):
     # the correlator norm runs over t for each channel: here over the sampled t
     C_ref = np.stack(C_ref, axis=-1)                                 # (16, n_sampled)
     assert corr_err(C[:, None, list(sampled)], C_ref[:, None, :]) <= TOL_F32
+
+
+# ---------------------------------------------------------------------------
+# growth beyond the FP32 range of the contractions: power-of-two rescaling
+
+
+@pytest.mark.parametrize("prec,tol", [("f32", TOL_F32), ("bf16", TOL_BF16)])
+def test_smearing_growth_rescaled_exactly(qdpg_gpu, prec, tol):
+    """kappa = 0.3, N = 60: the field grows by ~2^85 and its meson site
+    values (~2^170) would overflow FP32; the smearing rescales by exact
+    powers of two (the field's exp) and the contractions apply them to the
+    FP64 sums, so field and correlators still match the checker."""
+    q = qdpg_gpu
+    dims = (8, 8, 8, 4)
+    lat = q.Lattice(dims, 3)
+    U = fields.round_to_f32(fields.gauge_field(dims, 61, kind="near_unit"))
+    P = fields.round_to_f32(fields.propagator(dims, 62))
+    P_in = to_bf16_complex(P) if prec == "bf16" else P
+    Uf = make_field(q, lat, q.GAUGE, q.F32, U)
+    S = make_field(q, lat, q.PROPAGATOR, q.PREC_NAMES[prec], P_in)
+    q.gauss_smear(Uf, S, 0.3, 60, 3, scratch=S.like())
+    got = export(S)
+    ref = smear.gauss_smear(U, P_in, 0.3, 60, 3)
+    assert np.isfinite(got).all() and np.abs(ref).max() > 2.0 ** 70
+    assert field_err(got, ref) <= tol
+    C = q.meson_2pt(S, S, q.SIXTEEN_MESONS).cpu().numpy()
+    assert np.isfinite(C).all()
+    # the contraction of the field as stored (exact to FP32 site arithmetic)
+    assert corr_err(C, hadron.meson_2pt(got, got, hadron.SIXTEEN_MESONS)) <= TOL_F32
+    if prec == "f32":
+        assert corr_err(C, hadron.meson_2pt(ref, ref, hadron.SIXTEEN_MESONS)) <= TOL_F32
