@@ -18,6 +18,18 @@ device time per step, with inputs resident in HBM.  ``e2e`` is the same
 quantity through the public API with the inputs copied from pinned host
 memory and the correlators read back every step.
 
+Two further workloads are measured once each and reported under
+``components`` (``--no-batch``/``--no-scale`` skip them):
+
+  * ``batch``: 64 smearing + meson jobs of uneven lattice, N and kappa, FP32
+    one job at a time against batches replayed from CUDA graphs (FP32, BF16,
+    and float16 storage on the tensor-core hop), with the reduced-precision
+    correlator errors;
+  * ``scale_48x96``: eight 48^3x96 propagators smeared at (kappa, N) up to
+    (0.30, 80), all 8 x 8 meson pairs and the nucleon at 33 momenta, with
+    FP32 and with float16 storage, checked against the FP64 checker on a
+    sampled timeslice.
+
 ``--impl reference`` times the FP64 checker on the host cores on a bounded
 sample of the same workload (one timeslice per step).
 """
@@ -56,6 +68,8 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-job batched comparison (FP32 one job at a time vs batched FP32/BF16)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-scale", action="store_true",
+                    help="skip the 48^3x96 scale run (8 propagators, 64 meson pairs + nucleon at 33 momenta)")
     return ap.parse_args()
 
 
@@ -382,6 +396,113 @@ def batch_arms(q, dev, args) -> dict:
     }
 
 
+def scale_run(q, dev, args) -> dict:
+    """The 48^3x96 scale workload, one pass per storage: eight synthetic
+    propagators (device-generated, seeded), each smeared at its own
+    (kappa, N) in {(0.15,10), (0.20,20), (0.25,40), (0.30,80)} x {source,
+    sink}; then the sixteen mesons of all 8 x 8 propagator pairs and the
+    nucleon (u = propagator 0, d = propagator 1), each projected to the 33
+    momenta with |n|^2 <= 4, FP64 sums.  Once with FP32 propagators and
+    links (rescaled by exact powers of two where the growth needs it), once
+    with float16 propagators and float16 reconstruct-12 links on the
+    tensor-core hop.  Reports times, the float16 correlator error against
+    FP32, and the FP32 correlators of propagator 0 on timeslice 0 against
+    the FP64 checker (exact for a sample: the path never couples
+    timeslices)."""
+    import numpy as np
+    import torch
+
+    from oracle import hadron, smear
+    from synth import configs, device as synth_dev
+
+    torch.cuda.empty_cache()  # the batch comparison's fields are gone; return their memory
+    w = configs.SCALE_48x96
+    lat = q.Lattice(w.dims, w.j_decay)
+    kn = [pair for pair in w.extra["kappa_n"] for _ in ("src", "snk")]
+    moms = q.momenta_up_to(4)
+    V = lat.V
+    res = {"workload": w.name, "lattice": "48x48x48x96", "links": f"{w.links} SU(3) eps={w.eps}",
+           "props_kappa_n": kn, "n_mom": len(moms), "meson_pairs": len(kn) ** 2, "channels_per_pair": 16}
+
+    def ev():
+        return torch.cuda.Event(enable_timing=True)
+
+    corr, sample = {}, {}
+    for arm, up, pp, bpsi, blink in (("fp32", q.F32, q.F32, 1152, 216), ("f16_tc", q.F16_R12, q.F16, 576, 72)):
+        U_can = synth_dev.gauge_field(w.dims, w.seed, dev, kind=w.links, eps=w.eps)
+        U = q.Field(lat, q.GAUGE, up, device=dev).import_(U_can)
+        if arm == "fp32":
+            sample["U"] = U_can[:, :1].cpu().numpy()
+        del U_can
+        scratch = q.Field(lat, q.PROPAGATOR, pp, device=dev)
+        props, t_smear = [], 0.0
+        for i, (kappa, n) in enumerate(kn):
+            P_can = synth_dev.propagator(w.dims, w.seed + 17 * i, dev)
+            f = q.Field(lat, q.PROPAGATOR, pp, device=dev).import_(P_can)
+            if arm == "fp32" and i == 0:
+                sample["P"] = P_can[:1].cpu().numpy()
+            del P_can
+            torch.cuda.synchronize()
+            e0, e1 = ev(), ev()
+            e0.record()
+            q.gauss_smear(U, f, kappa, n, w.j_decay, scratch=scratch)
+            e1.record()
+            torch.cuda.synchronize()
+            t_smear += e0.elapsed_time(e1)
+            props.append(f)
+        del scratch
+        C = torch.empty((len(kn), len(kn), 16, len(moms), lat.Nt), dtype=torch.complex128, device=dev)
+        e0, e1 = ev(), ev()
+        e0.record()
+        for a in range(len(kn)):
+            for b in range(len(kn)):
+                q.meson_2pt(props[a], props[b], q.SIXTEEN_MESONS, moms, out=C[a, b])
+        Cn = q.baryon_2pt(props[0], props[1], q.NUCLEON, +1, moms)
+        e1.record()
+        torch.cuda.synchronize()
+        q.device_status()
+        t_con = e0.elapsed_time(e1)
+        corr[arm] = (C.cpu().numpy(), Cn.cpu().numpy())
+        hops = sum(n for _, n in kn)
+        res[arm] = {"smear_ms": t_smear, "contract_ms": t_con, "total_ms": t_smear + t_con, "hops": hops,
+                    "smear_gbs": hops * V * (2 * bpsi + blink) / (t_smear * 1e-3) / 1e9,
+                    "smear_fp32_equiv_gbs": hops * V * 2520 / (t_smear * 1e-3) / 1e9,
+                    "finite": bool(np.isfinite(corr[arm][0]).all() and np.isfinite(corr[arm][1]).all())}
+        del props, U, C, Cn
+        torch.cuda.empty_cache()
+
+    def corr_err(a, ref):
+        d = np.linalg.norm(a - ref, axis=-1)
+        nrm = np.linalg.norm(ref, axis=-1)
+        nrm = np.where(nrm > 1e-12 * nrm.max(), nrm, nrm.max())
+        return float((d / nrm).max())
+
+    (C32, N32), (C16, N16) = corr["fp32"], corr["f16_tc"]
+    res["speedup_f16_tc_vs_fp32"] = res["fp32"]["total_ms"] / res["f16_tc"]["total_ms"]
+    res["f16_vs_fp32_meson_corr_rel_err_max"] = max(corr_err(C16[a, b], C32[a, b])
+                                                    for a in range(len(kn)) for b in range(len(kn)))
+    res["f16_vs_fp32_nucleon_corr_rel_err"] = corr_err(N16, N32)
+    res["f16_tol"] = 2e-2
+    # FP32 against the checker: propagator 0 ((0.15, 10)) on timeslice 0, all 16 mesons at 33 momenta
+    t0 = time.perf_counter()
+    kappa0, n0 = kn[0]
+    S = smear.gauss_smear(sample["U"].astype(np.complex128), sample["P"].astype(np.complex128), kappa0, n0,
+                          w.j_decay)
+    ref = hadron.meson_2pt(S, S, hadron.SIXTEEN_MESONS, moms, j_decay=w.j_decay)
+    # scale of each momentum sum: A(t) = sum_x |c(x)| (a smooth field's p != 0
+    # correlators cancel strongly; FP32 site values bound the error relative to A)
+    A = np.stack([np.abs(hadron.meson_site(S, S, a, b)).sum(axis=(1, 2, 3)) for a, b in hadron.SIXTEEN_MESONS])
+    got = C32[0, 0][:, :, :1]
+    k0 = moms.index((0, 0, 0))
+    res["fp32_vs_checker"] = {
+        "sample": "propagator 0 (kappa 0.15, N 10), timeslice 0, 16 mesons x 33 momenta",
+        "p0_corr_rel_err": corr_err(got[:, k0:k0 + 1], ref[:, k0:k0 + 1]),
+        "err_rel_to_abs_site_sum": float((np.abs(got - ref)[..., 0] / A).max()),
+        "plain_corr_rel_err_all_p": corr_err(got, ref), "tol": 1e-5,
+        "checker_s": time.perf_counter() - t0}
+    return res
+
+
 def max_over_ranks(x: float, world: int, device) -> float:
     """Largest per-rank value (the slowest rank's time) on every rank."""
     if world == 1:
@@ -543,6 +664,9 @@ def gpu_arm(args):
     if not args.no_batch:
         batch = batch_arms(q, dev, args)
         components["batch"] = batch
+
+    if not args.no_scale and rank == 0:
+        components["scale_48x96"] = scale_run(q, dev, args)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -216,7 +216,7 @@ template <typename PsiT, int KIND, bool SITES>
 __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restrict__ Su, const PsiT* __restrict__ Sd,
                                                              Geom g, BaryonSpec B, BMoms M, double* __restrict__ out,
                                                              float2* __restrict__ sites, const ScaleRecord* ru,
-                                                             const ScaleRecord* rd) {
+                                                             const ScaleRecord* rd, int site_scale) {
   extern __shared__ float2 sm[];
   float2* su = sm;
   float2* sd = sm + kSites * kStride;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(kWarps * 32) baryon_kernel(const PsiT* __restr
     if constexpr (SITES) {
       if (lane == 0)
         sites[(long long)t * V3 + s3] =
-            scale_exp ? make_float2(ldexpf(acc.x, scale_exp), ldexpf(acc.y, scale_exp)) : acc;
+            (scale_exp && site_scale) ? make_float2(ldexpf(acc.x, scale_exp), ldexpf(acc.y, scale_exp)) : acc;
       continue;
     }
     if (lane == 0) {
@@ -356,7 +356,18 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
     }
 
   cudaStream_t s = as_stream(stream);
-  if (!sites) {
+  // Many momenta: unscaled site values to a temporary buffer, projected on
+  // the tensor cores with the fields' scale applied to the FP64 sums.
+  const bool tensor_proj = !sites && n_mom >= kTensorProjMinMom;
+  float2* ksites = sites;
+  int site_scale = 1;
+  if (tensor_proj) {
+    void* t = nullptr;
+    if (cudaMallocAsync(&t, sizeof(float2) * (size_t)g.Nt * g.V3, s) != cudaSuccess)
+      return fail(QDPG_ERR_NOMEM, "baryon_2pt: site values for the momentum projection");
+    ksites = static_cast<float2*>(t);
+    site_scale = 0;
+  } else if (!sites) {
     cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)n_mom * g.Nt, s);
     if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "baryon_2pt: memset: %s", cudaGetErrorString(e));
   }
@@ -365,16 +376,16 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
   ProfScope prof("baryon_2pt", s);
 #define QDPG_BARYON_LAUNCH(T, KIND)                                                                          \
   do {                                                                                                       \
-    if (sites) {                                                                                             \
+    if (ksites) {                                                                                            \
       auto k = baryon_kernel<T, KIND, true>;                                                                 \
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
       k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, \
-                                        M, out_dev, sites, Su->rec, Sd->rec);                                \
+                                        M, out_dev, ksites, Su->rec, Sd->rec, site_scale);                   \
     } else {                                                                                                 \
       auto k = baryon_kernel<T, KIND, false>;                                                                \
       cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
       k<<<grid, kWarps * 32, smem, s>>>(static_cast<const T*>(Su->data), static_cast<const T*>(Sd->data), g, B, \
-                                        M, out_dev, sites, Su->rec, Sd->rec);                                \
+                                        M, out_dev, ksites, Su->rec, Sd->rec, site_scale);                   \
     }                                                                                                        \
   } while (0)
   if (Su->prec == QDPG_BF16) {
@@ -388,7 +399,14 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
     else QDPG_BARYON_LAUNCH(float2, 1);
   }
 #undef QDPG_BARYON_LAUNCH
-  return check_launch("baryon_2pt");
+  int rc = check_launch("baryon_2pt");
+  if (tensor_proj) {
+    std::vector<int> mom_flat(moms, moms + 3 * (size_t)n_mom);
+    if (rc == QDPG_OK)
+      rc = launch_momproj(g, ksites, 1, mom_flat.data(), n_mom, origin, out_dev, Su->rec, 2, Sd->rec, 1, s);
+    cudaFreeAsync(ksites, s);
+  }
+  return rc;
 }
 
 }  // namespace

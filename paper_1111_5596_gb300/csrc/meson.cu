@@ -23,6 +23,7 @@
 // atomic per block and value.
 #include <cuda_fp16.h>
 
+#include <type_traits>
 #include <vector>
 
 #include "qdpg_internal.h"
@@ -70,26 +71,51 @@ struct SoASite {
   __device__ SoASite(const PsiT* S, int t, int s3, int V3_) : p(S + (long long)t * 144 * V3_ + s3), V3(V3_) {}
   __device__ __forceinline__ float2 operator()(int comp) const { return ld2(p + (long long)comp * V3); }
 };
-struct F16Site {
-  const __half2* p[3];
-  __device__ F16Site(const __half2* S, int t, int s3, int V3) {
-#pragma unroll
-    for (int vg = 0; vg < 3; ++vg) p[vg] = S + ((long long)(t * 3 + vg) * V3 + s3) * 48;
-  }
+// Float16 propagators are site-major, so a thread's own site is 576 strided
+// bytes: the block's sites are first staged in shared memory with coalesced
+// 16-byte loads, kF16Stride words per site (odd: conflict-free reads).
+constexpr int kF16Stride = 145;
+// Loaders of one site's float16 propagator: staged in shared memory (the
+// site's 145-word slot, vector groups 48 words apart) or in global memory.
+__device__ __forceinline__ float2 f16_word(uint32_t w) { return __half22float2(*reinterpret_cast<const __half2*>(&w)); }
+__device__ __forceinline__ int f16_site_word(int comp) {  // vector group * 48 + word within the group
+  const int sc = comp / 12, sp = comp % 12, sv = sc / 3, c = sc % 3;
+  const int v = sv * 12 + sp;
+  return (v >> 4) * 48 + (v & 15) * 3 + c;
+}
+struct F16Staged {
+  const uint32_t* p;
+  __device__ F16Staged(const uint32_t* slot) : p(slot) {}
+  __device__ __forceinline__ float2 operator()(int comp) const { return f16_word(p[f16_site_word(comp)]); }
+};
+struct F16Global {
+  const uint32_t* p;
+  long long gs;  // words between vector groups
+  __device__ F16Global(const uint32_t* S, int t, int s3, int V3)
+      : p(S + ((long long)t * 3 * V3 + s3) * 48), gs((long long)V3 * 48) {}
   __device__ __forceinline__ float2 operator()(int comp) const {
-    const int sc = comp / 12, sp = comp % 12, sv = sc / 3, c = sc % 3;
-    const int v = sv * 12 + sp;
-    return __half22float2(p[v >> 4][(v & 15) * 3 + c]);
+    const int w = f16_site_word(comp);
+    return f16_word(__ldg(p + (w / 48) * gs + w % 48));
   }
 };
-template <typename PsiT>
-struct SiteOf {
-  typedef SoASite<PsiT> type;
-};
-template <>
-struct SiteOf<__half2> {
-  typedef F16Site type;
-};
+
+// Stage words of sites s0 .. s0+127 (all three vector groups) of timeslice t.
+__device__ __forceinline__ void stage_f16(uint32_t* dst, const __half2* S, int t, int s0, int V3) {
+  const int nsite = min(kMesonThreads, V3 - s0);
+#pragma unroll
+  for (int vg = 0; vg < 3; ++vg) {
+    const uint4* src = reinterpret_cast<const uint4*>(S + ((long long)(t * 3 + vg) * V3 + s0) * 48);
+    for (int q = threadIdx.x; q < nsite * 12; q += kMesonThreads) {
+      const uint4 v = src[q];
+      const int i = q / 12, w = (q % 12) * 4;
+      uint32_t* d = dst + i * kF16Stride + vg * 48 + w;
+      d[0] = v.x;
+      d[1] = v.y;
+      d[2] = v.z;
+      d[3] = v.w;
+    }
+  }
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -99,11 +125,11 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // SITES: write each channel's site value c_j(x) to sites[row(j)][t][x]
 // (complex FP32) instead of reducing it.
-template <int NQ, typename PsiT, bool SITES>
+template <int NQ, typename PsiT, bool SITES, bool SAME>
 __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __restrict__ S1, const PsiT* __restrict__ S2,
                                                               Geom g, MesonPass P, Moms M, double* __restrict__ out,
                                                               float2* __restrict__ sites, const ScaleRecord* rec1,
-                                                              const ScaleRecord* rec2) {
+                                                              const ScaleRecord* rec2, int site_scale) {
   extern __shared__ double2 red[];  // [warp][nch * n_mom]
   const int s3 = blockIdx.x * kMesonThreads + threadIdx.x;
   const int t = blockIdx.y;
@@ -118,10 +144,18 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
 #pragma unroll
     for (int k = 0; k < 16; ++k) Q[q][k] = make_float2(0.f, 0.f);
 
-  // float16 storage: the value is the stored number times 2^exp per field
+  // the value is the stored number times 2^exp per field
   const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
-  if (live) {
-    const typename SiteOf<PsiT>::type p1(S1, t, s3, V3), p2(S2, t, s3, V3);
+  constexpr bool kF16 = std::is_same<PsiT, __half2>::value;
+  // float16: S2 (re-read by every mask pair) is staged in shared memory for
+  // the block's sites; S1 is read once per value, from the staged copy when
+  // S1 = S2 (SAME) and from global memory otherwise
+  uint32_t* st = reinterpret_cast<uint32_t*>(red + (SITES ? 0 : (kMesonThreads / 32) * nv));
+  if constexpr (kF16) {
+    stage_f16(st, reinterpret_cast<const __half2*>(S2), t, blockIdx.x * kMesonThreads, V3);
+    __syncthreads();
+  }
+  auto contract = [&](const auto& p1, const auto& p2) {
 #pragma unroll
     for (int al = 0; al < 4; ++al)
 #pragma unroll
@@ -150,6 +184,17 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
           Q[q][al * 4 + be] = acc;
         }
       }
+  };
+  if (live) {
+    if constexpr (kF16) {
+      const F16Staged p2(st + threadIdx.x * kF16Stride);
+      if constexpr (SAME)
+        contract(p2, p2);
+      else
+        contract(F16Global(reinterpret_cast<const uint32_t*>(S1), t, s3, V3), p2);
+    } else {
+      contract(SoASite<PsiT>(S1, t, s3, V3), SoASite<PsiT>(S2, t, s3, V3));
+    }
   }
 
   // exp(-i p.(x - x0)) needs the three non-decay coordinates
@@ -176,7 +221,7 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
       if constexpr (SITES) {
         if (live)
           sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] =
-              scale_exp ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
+              (scale_exp && site_scale) ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
       } else {
         for (int m = 0; m < M.n; ++m) {
           float2 v = c;
@@ -223,32 +268,36 @@ struct Channel {
 };
 
 int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
-                float2* sites, cudaStream_t s) {
+                float2* sites, cudaStream_t s, int site_scale = 1) {
   const Geom& g = S1->g;
   dim3 grid((g.V3 + kMesonThreads - 1) / kMesonThreads, g.Nt);
-  const size_t smem = sites ? 0 : (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
+  size_t smem = sites ? 0 : (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
   const bool bf = S1->prec == QDPG_BF16;
   const bool h16 = S1->prec == QDPG_F16;
+  const bool same = S1->data == S2->data;
+  if (h16) smem += (size_t)kMesonThreads * kF16Stride * sizeof(uint32_t);  // staged S2
   ProfScope prof("meson_2pt", s);
-#define QDPG_MESON_KERNEL(NQ, T, SITES)                                                                 \
+#define QDPG_MESON_KERNEL(NQ, T, SITES, SAME)                                                          \
   do {                                                                                                 \
-    auto k = meson_kernel<NQ, T, SITES>;                                                               \
+    auto k = meson_kernel<NQ, T, SITES, SAME>;                                                         \
     if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
     k<<<grid, kMesonThreads, smem, s>>>(static_cast<const T*>(S1->data), static_cast<const T*>(S2->data), g, P, M, \
-                                        out, sites, S1->rec, S2->rec);                                 \
+                                        out, sites, S1->rec, S2->rec, site_scale);                     \
   } while (0)
-#define QDPG_MESON_LAUNCH(NQ)                                       \
-  do {                                                              \
-    if (bf) {                                                       \
-      if (sites) QDPG_MESON_KERNEL(NQ, __nv_bfloat162, true);       \
-      else QDPG_MESON_KERNEL(NQ, __nv_bfloat162, false);            \
-    } else if (h16) {                                               \
-      if (sites) QDPG_MESON_KERNEL(NQ, __half2, true);              \
-      else QDPG_MESON_KERNEL(NQ, __half2, false);                   \
-    } else {                                                        \
-      if (sites) QDPG_MESON_KERNEL(NQ, float2, true);               \
-      else QDPG_MESON_KERNEL(NQ, float2, false);                    \
-    }                                                               \
+#define QDPG_MESON_LAUNCH(NQ)                                                  \
+  do {                                                                         \
+    if (bf) {                                                                  \
+      if (sites) QDPG_MESON_KERNEL(NQ, __nv_bfloat162, true, false);           \
+      else QDPG_MESON_KERNEL(NQ, __nv_bfloat162, false, false);                \
+    } else if (h16) {                                                          \
+      if (sites && same) QDPG_MESON_KERNEL(NQ, __half2, true, true);           \
+      else if (sites) QDPG_MESON_KERNEL(NQ, __half2, true, false);             \
+      else if (same) QDPG_MESON_KERNEL(NQ, __half2, false, true);              \
+      else QDPG_MESON_KERNEL(NQ, __half2, false, false);                       \
+    } else {                                                                   \
+      if (sites) QDPG_MESON_KERNEL(NQ, float2, true, false);                   \
+      else QDPG_MESON_KERNEL(NQ, float2, false, false);                        \
+    }                                                                          \
   } while (0)
   switch (P.nq) {
     case 1: QDPG_MESON_LAUNCH(1); break;
@@ -324,10 +373,43 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
     if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "meson_2pt: memset: %s", cudaGetErrorString(e));
   }
 
+  // Many momenta: the pass's site values (unscaled, pass-local rows) go to a
+  // temporary buffer and the tensor cores project them; the fields' scale is
+  // applied to the FP64 sums there.  Each channel's block of the output
+  // (n_mom x Nt) is then copied into place.
+  const bool tensor_proj = !sites && n_mom >= kTensorProjMinMom;
+  std::vector<int> mom_flat(3 * (size_t)n_mom);
+  for (int i = 0; i < 3 * n_mom; ++i) mom_flat[i] = moms[i];
   MesonPass P{};
   auto flush = [&]() -> int {
     if (P.nch == 0) return QDPG_OK;
-    int rc = launch_pass(P, M, S1, S2, out_dev, sites, s);
+    int rc = QDPG_OK;
+    if (!tensor_proj) {
+      rc = launch_pass(P, M, S1, S2, out_dev, sites, s);
+    } else {
+      MesonPass L = P;
+      for (int j = 0; j < L.nch; ++j) L.out_row[j] = j;
+      const size_t site_bytes = sizeof(float2) * (size_t)L.nch * g.Nt * g.V3;
+      const size_t out_bytes = sizeof(double) * 2 * (size_t)L.nch * n_mom * g.Nt;
+      void* tsites = nullptr;
+      void* tout = nullptr;
+      if (cudaMallocAsync(&tsites, site_bytes, s) != cudaSuccess || cudaMallocAsync(&tout, out_bytes, s) != cudaSuccess) {
+        if (tsites) cudaFreeAsync(tsites, s);
+        return fail(QDPG_ERR_NOMEM, "meson_2pt: %zu bytes of site values for the momentum projection", site_bytes);
+      }
+      rc = launch_pass(L, M, S1, S2, nullptr, static_cast<float2*>(tsites), s, 0);
+      if (rc == QDPG_OK)
+        rc = launch_momproj(g, tsites, L.nch, mom_flat.data(), n_mom, origin, static_cast<double*>(tout), S1->rec, 1,
+                            S2->rec, 1, s);
+      const size_t blk = sizeof(double) * 2 * (size_t)n_mom * g.Nt;
+      for (int j = 0; j < L.nch && rc == QDPG_OK; ++j) {
+        cudaError_t e = cudaMemcpyAsync(reinterpret_cast<char*>(out_dev) + blk * P.out_row[j],
+                                        static_cast<char*>(tout) + blk * j, blk, cudaMemcpyDeviceToDevice, s);
+        if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "meson_2pt: copy: %s", cudaGetErrorString(e));
+      }
+      cudaFreeAsync(tsites, s);
+      cudaFreeAsync(tout, s);
+    }
     P = MesonPass{};
     return rc;
   };

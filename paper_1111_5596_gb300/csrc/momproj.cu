@@ -33,8 +33,12 @@ constexpr int kChunk = 32;         // sites per staged chunk
 constexpr int kKt = 2 * kChunk;    // real K per chunk
 constexpr int kMaxMomP = 64;       // N = 2*n_mom <= 128
 constexpr int kTmemCols = 128;
+constexpr int kMaxAccSites = 256;  // sites summed in one FP32 tensor-core accumulator
 
 struct ProjArgs {
+  const ScaleRecord* ra;  // optional field scales: the sums are multiplied by
+  const ScaleRecord* rb;  // 2^(ca * ra->exp + cb * rb->exp) (null: 2^0)
+  int ca, cb;
   int rows;           // n_chan * Nt
   int Nt, V3, nmom, npad, sites_per_cta;
   int sL[3];
@@ -156,6 +160,7 @@ __global__ void __launch_bounds__(128, 1) momproj_kernel(const float2* __restric
     // epilogue: warp w owns TMEM lanes (rows) 32w..32w+31
     const int row = row0 + warp * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
+    const double scale = ldexp(1.0, (P.ra ? P.ca * P.ra->exp : 0) + (P.rb ? P.cb * P.rb->exp : 0));
     for (int c0 = 0; c0 < P.npad; c0 += 16) {
       float v[16];
       ptx::tmem_ld16(taddr + c0, v);
@@ -166,8 +171,8 @@ __global__ void __launch_bounds__(128, 1) momproj_kernel(const float2* __restric
           const int m = (c0 + i) / 2;
           if (m < P.nmom) {
             const long long o = ((long long)chan * P.nmom + m) * P.Nt + t;
-            atomicAdd(out + 2 * o, (double)v[i]);
-            atomicAdd(out + 2 * o + 1, (double)v[i + 1]);
+            atomicAdd(out + 2 * o, (double)v[i] * scale);
+            atomicAdd(out + 2 * o + 1, (double)v[i + 1] * scale);
           }
         }
       }
@@ -185,18 +190,22 @@ __global__ void __launch_bounds__(128, 1) momproj_kernel(const float2* __restric
 
 using namespace qdpg;
 
-extern "C" int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, int n_chan, const int* moms,
-                                     int n_mom, const int origin[4], double* out_dev, void* stream) {
-  if (!lat || !sites_dev || !moms || !out_dev) return fail(QDPG_ERR_ARG, "momentum_project: null argument");
+namespace qdpg {
+
+int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* moms, int n_mom, const int origin[4],
+                   double* out_dev, const ScaleRecord* ra, int ca, const ScaleRecord* rb, int cb, cudaStream_t s) {
   if (n_chan < 1) return fail(QDPG_ERR_ARG, "momentum_project: n_chan %d < 1", n_chan);
   if (n_mom < 1 || n_mom > kMaxMomP) return fail(QDPG_ERR_ARG, "momentum_project: n_mom %d outside 1..%d", n_mom, kMaxMomP);
   if (reinterpret_cast<uintptr_t>(sites_dev) % 8) return fail(QDPG_ERR_ARG, "momentum_project: sites not 8-byte aligned");
-  const Geom& g = lat->g;
   const long long rows = (long long)n_chan * g.Nt;
   if (rows > (1LL << 30)) return fail(QDPG_ERR_ARG, "momentum_project: too many rows");
   unsigned int* status = device_status_word();
   if (!status) return fail(QDPG_ERR_CUDA, "momentum_project: no status word");
   ProjArgs P{};
+  P.ra = ra;
+  P.rb = rb;
+  P.ca = ca;
+  P.cb = cb;
   P.rows = (int)rows;
   P.Nt = g.Nt;
   P.V3 = g.V3;
@@ -209,13 +218,16 @@ extern "C" int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, 
   for (int m = 0; m < n_mom; ++m)
     for (int k = 0; k < 3; ++k) P.k[m][k] = moms[3 * m + k];
   const int row_tiles = (int)((rows + kM - 1) / kM);
-  // split the sites so that about two waves of CTAs run; at least 32 sites each
+  // split the sites so that about two waves of CTAs run; at least 32 sites
+  // each, and at most kMaxAccSites: the tensor-core accumulator is FP32, so
+  // its depth bounds the rounding error; longer sums go through the FP64
+  // atomics across CTAs
   int nsplit = std::max(1, std::min((g.V3 + kChunk - 1) / kChunk, (2 * 152 + row_tiles - 1) / row_tiles));
+  nsplit = std::max(nsplit, (g.V3 + kMaxAccSites - 1) / kMaxAccSites);
   P.sites_per_cta = ((g.V3 + nsplit - 1) / nsplit + kChunk - 1) / kChunk * kChunk;
   nsplit = (g.V3 + P.sites_per_cta - 1) / P.sites_per_cta;
   const size_t smem = (size_t)2 * kM * kKt * 4 + (size_t)2 * P.npad * kKt * 4 + 16;
 
-  cudaStream_t s = as_stream(stream);
   cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)rows * n_mom, s);
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "momentum_project: memset: %s", cudaGetErrorString(e));
   e = cudaFuncSetAttribute(momproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -225,4 +237,13 @@ extern "C" int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, 
   momproj_kernel<<<grid, 128, smem, s>>>(static_cast<const float2*>(sites_dev), P, out_dev, status,
                                          wait_timeout_ns());
   return check_launch("momentum_project");
+}
+
+}  // namespace qdpg
+
+extern "C" int qdpg_momentum_project(qdpg_lattice_t lat, const void* sites_dev, int n_chan, const int* moms,
+                                     int n_mom, const int origin[4], double* out_dev, void* stream) {
+  if (!lat || !sites_dev || !moms || !out_dev) return fail(QDPG_ERR_ARG, "momentum_project: null argument");
+  return launch_momproj(lat->g, sites_dev, n_chan, moms, n_mom, origin, out_dev, nullptr, 0, nullptr, 0,
+                        as_stream(stream));
 }

@@ -147,6 +147,13 @@ RescalePlan rescale_plan(double kappa, int n_iter);
 // data *= 2^-shift elementwise (F32 or BF16 storage); rec->exp += shift.
 int launch_rescale(void* data, int prec, long long nelem, int shift, ScaleRecord* rec, cudaStream_t s);
 
+// Tensor-core momentum projection of site values (momproj.cu); the sums are
+// multiplied by 2^(ca * ra->exp + cb * rb->exp) (null records: 2^0).
+int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* moms, int n_mom, const int origin[4],
+                   double* out_dev, const ScaleRecord* ra, int ca, const ScaleRecord* rb, int cb, cudaStream_t s);
+// meson_2pt/baryon_2pt with at least this many momenta project on the tensor cores.
+constexpr int kTensorProjMinMom = 8;
+
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
 // Device-side helpers --------------------------------------------------------

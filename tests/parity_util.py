@@ -36,3 +36,18 @@ def to_bf16_complex(a: np.ndarray) -> np.ndarray:
     re = t.real.to(torch.float32).to(torch.bfloat16).to(torch.float64)
     im = t.imag.to(torch.float32).to(torch.bfloat16).to(torch.float64)
     return torch.complex(re, im).numpy()
+
+
+def proj_err(C, C_ref, abs_scale) -> float:
+    """Error of momentum-projected correlators C[..., p, t] measured against
+    the scale of the sum that produced them: per (channel, momentum),
+    ||C - C_ref||_2 over t divided by ||A||_2 over t, where A(t) =
+    sum_x |c(x)| is the sum of the site values' magnitudes (the same for
+    every momentum).  At p != 0 a smooth field's correlator is a heavily
+    cancelling sum, and FP32 site values bound the accuracy of any such sum
+    relative to A, not to the (much smaller) result."""
+    C = np.asarray(C)
+    C_ref = np.asarray(C_ref)
+    A = np.asarray(abs_scale)
+    diff = np.linalg.norm(C - C_ref, axis=-1)
+    return float((diff / np.linalg.norm(A, axis=-1)[..., None]).max())

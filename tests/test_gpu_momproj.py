@@ -5,7 +5,7 @@ import torch
 
 from oracle import baryon, hadron
 from synth import fields
-from tests.parity_util import TOL_F32, corr_err
+from tests.parity_util import TOL_F32, corr_err, proj_err
 
 pytestmark = pytest.mark.gpu
 
@@ -66,3 +66,38 @@ def test_mesons_and_baryons_at_33_momenta(qdpg_gpu):
         Cb = q.momentum_project(lat, sv.reshape(1, dims[3], -1), moms).cpu().numpy()
         refb = baryon.baryon_2pt(S1, S2, kind, +1, moms)
         assert corr_err(Cb, refb[None]) <= TOL_F32, kind
+
+
+def test_meson_and_baryon_2pt_many_momenta_on_tensor_cores(qdpg_gpu):
+    """meson_2pt / baryon_2pt with 8 or more momenta project on the tensor
+    cores internally; with an origin, a 33-momentum set, and a smeared
+    field rescaled by powers of two (kappa = 0.3, N = 40) whose cube exceeds
+    the FP32 range of the contractions, they match the checker."""
+    from oracle import smear
+
+    q = qdpg_gpu
+    dims = (6, 6, 6, 4)
+    lat = q.Lattice(dims, 3)
+    U = fields.round_to_f32(fields.gauge_field(dims, 32, kind="near_unit"))
+    P1 = fields.round_to_f32(fields.propagator(dims, 33, envelope=0.3))
+    P2 = fields.round_to_f32(fields.propagator(dims, 34, envelope=0.3))
+    Uf = q.Field(lat, q.GAUGE, q.F32, device="cuda:0").import_(torch.from_numpy(U.astype(np.complex64)).to("cuda:0"))
+    f1, f2 = _prop(q, lat, P1), _prop(q, lat, P2)
+    q.gauss_smear(Uf, f1, 0.3, 40, 3, scratch=f1.like())
+    S1 = smear.gauss_smear(U, P1, 0.3, 40, 3)
+    assert np.abs(S1).max() > 2.0 ** 50          # the Delta's three factors of S1 exceed the FP32 range
+    moms, origin = q.momenta_up_to(4), (1, 0, 2, 3)
+    C = q.meson_2pt(f1, f2, q.SIXTEEN_MESONS, moms, origin=origin).cpu().numpy()
+    ref = hadron.meson_2pt(S1, P2, hadron.SIXTEEN_MESONS, moms, origin=origin)
+    assert np.isfinite(C).all()
+    # smeared fields are smooth: errors relative to sum_x |c(x)| per t (proj_err)
+    A = np.stack([np.abs(hadron.meson_site(S1, P2, a, b)).sum(axis=(1, 2, 3)) for a, b in hadron.SIXTEEN_MESONS])
+    assert proj_err(C, ref, A) <= TOL_F32
+    assert corr_err(C[:, :1], ref[:, :1]) <= TOL_F32          # zero momentum: no cancellation
+    for kind, K in (("nucleon", q.NUCLEON), ("delta", q.DELTA)):
+        Sd = P2 if kind == "nucleon" else S1
+        Cb = q.baryon_2pt(f1, f2 if kind == "nucleon" else None, K, -1, moms, origin=origin).cpu().numpy()
+        refb = baryon.baryon_2pt(S1, Sd, kind, -1, moms, origin=origin)
+        Ab = np.abs(baryon.baryon_site(S1, Sd, kind, -1)).sum(axis=(1, 2, 3))
+        assert np.isfinite(Cb).all()
+        assert proj_err(Cb[None], refb[None], Ab[None]) <= TOL_F32, kind
