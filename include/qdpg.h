@@ -162,7 +162,7 @@ int qdpg_device_status(void* stream);
  *  QDPG_DEBUG_FORCE_SIMPLE_HOP nonzero: always use the one-thread-per-site
  *                              smearing kernel without the copy pipeline;
  * and launch-shape settings of the pipelined smearing kernel:
- *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..256, 0 = default;
+ *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..288, 0 = default;
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
  *  QDPG_TUNE_GRID              0: persistent CTAs (default), 1: one CTA per item;
  * and of the float16 (tensor-core) smearing kernel:

@@ -187,12 +187,12 @@ int qdpg_tune_smear(qdpg_field_t U, qdpg_field_t psi, qdpg_field_t scratch, int 
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
     return fail(QDPG_ERR_CUDA, "tune_smear: event creation failed");
-  static const int consumer_opts[] = {256, 192, 128, 96, 64, 48, 32};
+  static const int consumer_opts[] = {288, 256, 192, 128, 96, 64, 48, 32};
   TileCfg best{0, 0, 0};
   float best_us = 0.f;
   int last_k = -1;
   int rc = QDPG_OK;
-  for (int ci = 0; ci < 7 && rc == QDPG_OK; ++ci) {
+  for (int ci = 0; ci < 8 && rc == QDPG_OK; ++ci) {
     // skip widths that give the same tile as the previous one
     int kk = 0;
     for (int d = 1; d <= g.sL[1]; ++d)
@@ -270,7 +270,7 @@ int qdpg_tune_load(const char* path) {
     if (sscanf(line, "%d %d %d %d %d %d %d %d %d %d %f", &k.L[0], &k.L[1], &k.L[2], &k.L[3], &k.jd, &k.psi,
                &k.link, &c.consumers, &c.grid_mode, &c.stages, &us) != 11)
       continue;
-    if (c.consumers < 32 || c.consumers > 256 || c.grid_mode < 0 || c.grid_mode > 1 || c.stages < 0 || c.stages > 16)
+    if (c.consumers < 32 || c.consumers > tma_smear::kMaxConsumers || c.grid_mode < 0 || c.grid_mode > 1 || c.stages < 0 || c.stages > 16)
       continue;
     g_tune[k] = {c, us};
     ++n;

@@ -41,7 +41,7 @@ namespace tma_smear {
 using namespace smear_dev;
 
 constexpr int kMaxStages = 16;
-constexpr int kMaxConsumers = 256;
+constexpr int kMaxConsumers = 288;
 constexpr int kSplit = 2;  // work items per tile: colour vectors 0..23 and 24..47
 
 // Shared-memory loads of staged elements (plain loads: __ldg is global-only).
@@ -423,6 +423,8 @@ int launch_tma_t(const HopLaunch& a) {
   X(24, 4, 1)                    \
   X(48, 4, 1)                    \
   X(48, 2, 1)                    \
+  X(24, 12, 1)                   \
+  X(48, 6, 1)                    \
   X(8, 8, 0)                     \
   X(12, 12, 0)
 

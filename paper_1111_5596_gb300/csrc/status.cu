@@ -81,8 +81,8 @@ int qdpg_debug_set(int what, long long value) {
       g_force_simple = value != 0;
       return ok();
     case QDPG_TUNE_TILE_CONSUMERS:
-      if (value != 0 && (value < 32 || value > 256))
-        return fail(QDPG_ERR_ARG, "debug_set: tile consumers outside 32..256 (0 = default)");
+      if (value != 0 && (value < 32 || value > 288))
+        return fail(QDPG_ERR_ARG, "debug_set: tile consumers outside 32..288 (0 = default)");
       g_tile_consumers = (int)value;
       return ok();
     case QDPG_TUNE_STAGES:

@@ -15,10 +15,22 @@ def _field(q, lat, kind, prec, canon):
     return q.Field(lat, kind, prec, device="cuda:0").import_(torch.from_numpy(canon.astype(np.complex64)).to("cuda:0"))
 
 
-@pytest.mark.parametrize("dims,prec", [((16, 16, 16, 4), "f32"), ((8, 12, 6, 3), "f32"), ((24, 24, 8, 2), "f32"),
-                                       ((8, 8, 8, 4), "bf16"), ((12, 6, 4, 2), "bf16")])
-def test_pipelined_equals_simple_kernel(qdpg_gpu, dims, prec):
+@pytest.mark.parametrize("dims,prec,sites", [((16, 16, 16, 4), "f32", 0), ((8, 12, 6, 3), "f32", 0),
+                                             ((24, 24, 8, 2), "f32", 0), ((24, 24, 4, 2), "f32", 288),
+                                             ((48, 12, 3, 2), "bf16", 288), ((8, 8, 8, 4), "bf16", 0),
+                                             ((12, 6, 4, 2), "bf16", 0)])
+def test_pipelined_equals_simple_kernel(qdpg_gpu, dims, prec, sites):
+    """sites: most sites per tile (0 = default); 288 gives 12-row tiles at
+    Lx = 24 and 6-row tiles at Lx = 48."""
     q = qdpg_gpu
+    q.debug_set(q.TUNE_TILE_CONSUMERS, sites)
+    try:
+        _pipelined_vs_simple(q, dims, prec)
+    finally:
+        q.debug_set(q.TUNE_TILE_CONSUMERS, 0)
+
+
+def _pipelined_vs_simple(q, dims, prec):
     lat = q.Lattice(dims, 3)
     U = fields.round_to_f32(fields.gauge_field(dims, 31, kind="haar"))
     psi = fields.round_to_f32(fields.propagator(dims, 31, envelope=0.3))
@@ -76,7 +88,7 @@ def test_autotuner_picks_a_config_and_keeps_parity(qdpg_gpu, tmp_path):
     Uf = _field(q, lat, q.GAUGE, q.F32, U)
     f = _field(q, lat, q.PROPAGATOR, q.F32, psi)
     sites, grid_mode, us = q.tune_smear(Uf, f, f.like(), reps=2)
-    assert 32 <= sites <= 256 and grid_mode in (0, 1) and us > 0
+    assert 32 <= sites <= 288 and grid_mode in (0, 1) and us > 0
     # psi is only read by the tuner
     assert np.array_equal(f.export().cpu().numpy(), psi)
     q.gauss_smear(Uf, f, 0.2, 4, scratch=f.like())
