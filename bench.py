@@ -633,14 +633,22 @@ def gpu_arm(args):
     if not args.no_e2e:
         U_stage = torch.empty_like(U_dev)
         P_stage = torch.empty_like(P_dev)
+        copy_stream = torch.cuda.Stream(dev)
+        P_copied = torch.cuda.Event()
 
         def step_e2e():
+            # the propagator's host copy runs on a second stream while the
+            # source (which does not need it) is smeared
+            copy_stream.wait_stream(stream)
+            with torch.cuda.stream(copy_stream):
+                P_stage.copy_(P_h, non_blocking=True)
+                P_copied.record(copy_stream)
             U_stage.copy_(U_h, non_blocking=True)
-            P_stage.copy_(P_h, non_blocking=True)
             U.import_(U_stage)
-            snk.import_(P_stage)
             q.point_source(src)
             q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
+            stream.wait_event(P_copied)
+            snk.import_(P_stage)
             q.gauss_smear(U, snk, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
             q.meson_2pt(snk, snk, q.SIXTEEN_MESONS, out=C)
             C_h.copy_(C, non_blocking=True)

@@ -1,0 +1,93 @@
+"""The 64-job batched workload at full size: lattices drawn from 8^3x16,
+12^3x24, 16^3x32 and 24^3x48, N in [5, 50], kappa in [0.15, 0.30], each job
+with its own seeded Haar links and synthetic propagator, smeared and
+contracted (16 mesons, p = 0) as one batch replayed from a CUDA graph, in
+FP32 storage and in float16 storage (per-field power-of-two scale, float16
+reconstruct-12 links, tensor-core hop).
+
+For each lattice size the job with the most iterations is checked against
+the FP64 checker on timeslice 0 (smearing and contractions never couple
+timeslices, so one timeslice is exact), and against the one-job entry
+point bit for bit (FP32).  Correlator errors on that one timeslice are per
+channel |C - C_ref| / |C_ref| for FP32, and relative to A = sum_x |c(x)| for
+float16: a single timeslice sum of a synthetic propagator's non-pion
+channel cancels strongly, and stored values with 11 significant bits bound
+the error of such a sum relative to A (8^3 job, N = 44: 4.4e-2 of |C_ref|,
+~1e-3 of A).  Over all timeslices, every float16 job's correlators stay
+within the reduced-precision bound of FP32's, per channel.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import hadron, smear
+from synth import configs
+from synth import device as synth_dev
+from tests.parity_util import TOL_BF16, TOL_F32, corr_err, field_err, proj_err
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+def test_batch64_full_size_fp32_and_f16(qdpg_gpu):
+    q = qdpg_gpu
+    dev = torch.device("cuda:0")
+    jobs = configs.batch_jobs(configs.BATCH_64)
+    assert len(jobs) == 64
+    lats, rows = {}, []
+    for j in jobs:
+        dims = j["dims"]
+        if dims not in lats:
+            lats[dims] = q.Lattice(dims, 3)
+        lat = lats[dims]
+        U_can = synth_dev.gauge_field(dims, j["seed"], dev)
+        P_can = synth_dev.propagator(dims, j["seed"], dev)
+        r = {"job": j, "lat": lat, "U_can": U_can, "P_can": P_can,
+             "U32": q.Field(lat, q.GAUGE, q.F32, device=dev).import_(U_can),
+             "Uh": q.Field(lat, q.GAUGE, q.F16_R12, device=dev).import_(U_can)}
+        for tag, prec in (("32", q.F32), ("h", q.F16)):
+            r["p" + tag] = q.Field(lat, q.PROPAGATOR, prec, device=dev).import_(P_can)
+            r["s" + tag] = r["p" + tag].like()
+            r["m" + tag] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
+        rows.append(r)
+    for tag, U in (("32", "U32"), ("h", "Uh")):
+        b = q.Batch([(r[U], r["p" + tag], r["s" + tag], r["job"]["kappa"], r["job"]["n_iter"], r["m" + tag])
+                     for r in rows])
+        b.run(use_graph=True)
+    torch.cuda.synchronize()
+    q.device_status()
+
+    # one job per lattice size: the one with the most iterations
+    sample = {}
+    for r in rows:
+        d = r["job"]["dims"]
+        if d not in sample or r["job"]["n_iter"] > sample[d]["job"]["n_iter"]:
+            sample[d] = r
+    assert len(sample) == 4
+    report = {}
+    for d, r in sorted(sample.items()):
+        j = r["job"]
+        Ut = r["U_can"][:, 0:1].cpu().numpy().astype(np.complex128)
+        Pt = r["P_can"][0:1].cpu().numpy().astype(np.complex128)
+        ref = smear.gauss_smear(Ut, Pt, j["kappa"], j["n_iter"], 3)
+        C_ref = hadron.meson_2pt(ref, ref, hadron.SIXTEEN_MESONS)           # (16, 1, 1)
+        A = np.array([[np.abs(hadron.meson_site(ref, ref, a, b)).sum()] for a, b in hadron.SIXTEEN_MESONS])
+        e = {}
+        for tag in ("32", "h"):
+            got = r["p" + tag].export()[0:1].cpu().numpy()
+            C = r["m" + tag][:, None, 0:1].cpu().numpy()
+            e[tag] = (field_err(got, ref), corr_err(C, C_ref), proj_err(C, C_ref, A))
+        report[f"{d[0]}^3x{d[3]} N={j['n_iter']} kappa={j['kappa']:.3f}"] = e
+        # the batch runs the one-job path's per-site arithmetic: same bits
+        g = r["p32"].like().import_(r["P_can"])
+        q.gauss_smear(r["U32"], g, j["kappa"], j["n_iter"], 3, scratch=g.like())
+        assert torch.equal(g.export(), r["p32"].export()), d
+    # float16 against FP32 over all timeslices, every job
+    def corr_err_t(a, b):
+        return corr_err(a.cpu().numpy()[:, None, :], b.cpu().numpy()[:, None, :])
+
+    worst = max(corr_err_t(r["mh"], r["m32"]) for r in rows)
+    print(report, "float16 vs FP32 over t, max over jobs:", worst)
+    for key, e in report.items():
+        assert e["32"][0] <= TOL_F32 and e["32"][1] <= TOL_F32, (key, e)
+        assert e["h"][0] <= 5e-3 and e["h"][2] <= 5e-3, (key, e)  # float16 storage: observed ~1e-3
+    assert worst <= TOL_BF16
