@@ -637,13 +637,14 @@ def gpu_arm(args):
         P_copied = torch.cuda.Event()
 
         def step_e2e():
-            # the propagator's host copy runs on a second stream while the
-            # source (which does not need it) is smeared
+            # the links first (host-to-device copies share a copy engine in
+            # issue order); the propagator's copy then runs on a second stream
+            # while the source, which does not need it, is smeared
+            U_stage.copy_(U_h, non_blocking=True)
             copy_stream.wait_stream(stream)
             with torch.cuda.stream(copy_stream):
                 P_stage.copy_(P_h, non_blocking=True)
                 P_copied.record(copy_stream)
-            U_stage.copy_(U_h, non_blocking=True)
             U.import_(U_stage)
             q.point_source(src)
             q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
