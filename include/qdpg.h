@@ -166,7 +166,10 @@ int qdpg_device_status(void* stream);
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
  *  QDPG_TUNE_GRID              0: persistent CTAs (default), 1: one CTA per item;
  * and of the float16 (tensor-core) smearing kernel:
- *  QDPG_TUNE_F16_WARPS         consumer warps per CTA, 8 or 16 (0 = default, 16). */
+ *  QDPG_TUNE_F16_WARPS         consumer warps per CTA, 8 or 16 (0 = default, 16);
+ *  QDPG_TUNE_TENSOR_COPY       FP32/BF16 pipelined hop: 0 (default) stages whole-plane
+ *                              tiles with one tensor-map (TMA) copy per stage where
+ *                              planes z-1..z+1 are consecutive, 1 uses bulk copies only. */
 enum {
   QDPG_DEBUG_WAIT_TIMEOUT_NS = 1,
   QDPG_DEBUG_DROP_STAGE = 2,
@@ -174,7 +177,8 @@ enum {
   QDPG_TUNE_TILE_CONSUMERS = 4,
   QDPG_TUNE_STAGES = 5,
   QDPG_TUNE_GRID = 7,
-  QDPG_TUNE_F16_WARPS = 8
+  QDPG_TUNE_F16_WARPS = 8,
+  QDPG_TUNE_TENSOR_COPY = 9
 };
 int qdpg_debug_set(int what, long long value);
 

@@ -1,5 +1,5 @@
-// Inline-PTX helpers for sm_103a: mbarrier, bulk async copies (TMA engine),
-// and bounded waits.  Every wait here gives up after a deadline measured on
+// Inline-PTX helpers for sm_103a: mbarrier, bulk and tensor-map async copies
+// (TMA engine), and bounded waits.  Every wait here gives up after a deadline measured on
 // %globaltimer and reports that to its caller instead of spinning forever.
 #pragma once
 
@@ -80,6 +80,20 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t
   asm volatile(
       "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
       "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// Tiled tensor copy global -> shared of one 4-D box described by a tensor
+// map (TMA), completing the box's bytes of transaction count on the
+// mbarrier.  `tmap` is the address of a CUtensorMap in kernel-parameter,
+// constant or global memory; dst is 128-byte aligned; c0 (the innermost
+// coordinate) times the element size is a multiple of 16 bytes.
+__device__ __forceinline__ void tensor_g2s_4d(uint32_t dst, const void* tmap, int c0, int c1, int c2, int c3,
+                                              uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];" ::"r"(dst),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
 

@@ -101,6 +101,7 @@ bool debug_force_simple_hop();
 int debug_tile_consumers();  // max consumer threads per pipelined tile, 0 = per-geometry default
 int debug_tile_stages();     // pipeline depth, 0 = as many as fit the shared-memory budget
 int debug_tile_grid();       // 0: persistent CTAs, 1: one CTA per work item
+int debug_tensor_copy_off();  // 1: no tensor-map copies in the pipelined FP32/BF16 hop
 int debug_f16_warps();       // consumer warps of the float16 smearing kernel, 0 = default
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage

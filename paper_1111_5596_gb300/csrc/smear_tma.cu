@@ -65,9 +65,14 @@ bool pick_tile(const Geom& g, int esize, int link_esize, int link_ne, int max_co
   return true;
 }
 
-// Default tile width: whole 16x16 planes; narrower tiles on wide planes,
-// where smaller CTAs (several per SM) measured faster on GB300.
-int default_consumers(const Geom& g) { return g.sL[0] >= 24 ? 128 : 256; }
+// Default tile width: whole 16x16 planes; on wide planes (Lx >= 24) tiles
+// of up to 288 sites for FP32 propagators (one CTA of nine consumer warps
+// per SM) and of up to 128 for BF16 (several CTAs per SM), the faster
+// choices measured on GB300.
+int default_consumers(const Geom& g, int psi_prec) {
+  if (g.sL[0] < 24) return 256;
+  return psi_prec == QDPG_F32 ? 288 : 128;
+}
 
 
 // ---- launch configuration and the autotuning table ---------------------------
@@ -98,6 +103,42 @@ TuneKey key_of(const Geom& g, int psi_prec, int lprec) {
   return k;
 }
 
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point
+// (the library links the runtime only).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+// The input propagator of one job as the 4-D tensor of the whole-plane
+// tensor-map copies: (x; row = y + Ly*z; the 12 colour vectors of a spin
+// row, stride V3; spin-row-colour + 12*t, stride 12*V3), box (Lx, 3k rows
+// = planes z-1..z+1, G vectors, 3 colours) = one stage.
+bool encode_psi_map(CUtensorMap* m, const void* in, const Geom& g, int esize, int k, int G) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t Lx = g.sL[0], V3 = g.V3;
+  const cuuint64_t dims[4] = {Lx, (cuuint64_t)g.sL[1] * g.sL[2], 12, 12 * (cuuint64_t)g.Nt};
+  const cuuint64_t strides[3] = {Lx * esize, V3 * esize, 12 * V3 * esize};
+  const cuuint32_t box[4] = {(cuuint32_t)Lx, (cuuint32_t)(3 * k), (cuuint32_t)G, 3};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+            const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The configuration a launch uses: explicit tuning settings first, then the
 // autotuning table, then the defaults.
 TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
@@ -108,7 +149,7 @@ TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
     auto it = g_tune.find(key_of(g, psi_prec, lprec));
     if (it != g_tune.end()) return it->second.first;
   }
-  if (!c.consumers) c.consumers = default_consumers(g);
+  if (!c.consumers) c.consumers = default_consumers(g, psi_prec);
   return c;
 }
 
@@ -126,6 +167,16 @@ int launch_hop_tma_cfg(const tma_smear::JobPtrs* jobs, int njobs, int lprec, int
   if (!a.status) return QDPG_ERR_UNSUPPORTED;
   a.jobs.njobs = njobs;
   for (int i = 0; i < njobs; ++i) a.jobs.j[i] = jobs[i];
+  // whole-plane tiles whose stages are one box: tensor-map copies where
+  // planes z-1..z+1 are consecutive (1 <= z <= Lz-2)
+  const int esize = bf ? 4 : 8;
+  const size_t stage_bytes = (size_t)a.tt.G * 3 * a.tt.rows * g.sL[0] * esize;
+  a.tt.use_tmap = !debug_tensor_copy_off() && !a.tt.halo && g.sL[2] >= 3 && 3 * a.tt.k <= 256 && g.sL[0] <= 256 &&
+                  stage_bytes % 128 == 0;
+  for (int i = 0; i < njobs && a.tt.use_tmap; ++i)
+    if (reinterpret_cast<uintptr_t>(jobs[i].in) % 16 != 0 ||
+        !encode_psi_map(&a.jobs.tmap[i], jobs[i].in, g, esize, a.tt.k, a.tt.G))
+      a.tt.use_tmap = 0;
   a.g = g;
   a.timeout_ns = wait_timeout_ns();
   a.drop_stage = debug_drop_vector();

@@ -11,13 +11,17 @@
 //    flight together and share their halo reads in L2;
 //  * each consumer thread owns one site and keeps its six links in registers
 //    for the item's 24 colour vectors;
-//  * one producer warp streams, with bulk asynchronous copies (cp.async.bulk
-//    on the TMA engine), first the links of the item's tile into a
-//    shared-memory link buffer, then G colour vectors per stage of the three
-//    colour planes of the tile plus its halo (rows y0-1 and y0+k of plane z
-//    unless the tile is a whole plane, and the same k rows of planes z-1 and
-//    z+1, all periodic); it runs ahead of the consumers across item
-//    boundaries, so consumers never wait on global loads;
+//  * one producer warp streams, with asynchronous copies on the TMA engine,
+//    first the links of the item's tile into a shared-memory link buffer
+//    (cp.async.bulk), then G colour vectors per stage of the three colour
+//    planes of the tile plus its halo (rows y0-1 and y0+k of plane z unless
+//    the tile is a whole plane, and the same k rows of planes z-1 and z+1,
+//    all periodic), each run of consecutive rows in one copy; a whole-plane
+//    tile whose planes z-1..z+1 are consecutive in memory takes the whole
+//    stage in one tensor-map copy (cp.async.bulk.tensor, a 4-D box); it runs
+//    ahead of the consumers across item boundaries, so consumers never wait
+//    on global loads.  A stage holds region (colour q, vector gg) at
+//    (q * G + gg) * rows * Lx, rows in the order the copies deliver them;
 //  * mbarriers hand stages and the link buffer between producer and
 //    consumers ("full" with a transaction count, "empty" with one arrival per
 //    consumer warp); every wait is bounded, and a wait that runs out records
@@ -27,6 +31,8 @@
 //    template constants, so every shared-memory operand is a register base
 //    plus an immediate offset.
 #pragma once
+
+#include <cuda.h>  // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
 
 #include <type_traits>
 
@@ -62,6 +68,7 @@ struct TmaTile {
   int nitems;     // tiles * kSplit
   int grid;       // persistent CTAs
   int smem;       // dynamic shared memory bytes
+  int use_tmap;   // 1: whole-plane tiles stage planes z-1..z+1 with one tensor-map copy
 };
 
 // Jobs of one launch: same lattice and precisions, own fields and kappa.
@@ -73,9 +80,13 @@ struct JobPtrs {
   const void* U;
   float kappa;
 };
+// tmap[i]: job i's input propagator as a 4-D tensor (x; row = y + Ly*z;
+// the 12 colour vectors of a spin row; spin-row-colour + 12*t), for the
+// whole-plane tiles' tensor-map copies (TmaTile::use_tmap).
 struct JobTable {
   int njobs;
   JobPtrs j[kMaxJobs];
+  CUtensorMap tmap[kMaxJobs];
 };
 
 struct HopLaunch {
@@ -202,8 +213,6 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
 
   if (warp == tt.cwarps) {
     // ---------------- producer warp ----------------
-    const int npieces = halo ? 5 : 3;
-    const int ncopies = G * 3 * npieces;
     const int nlcopies = 4 * NE + (halo ? NE : 0);
     int gstage = 0, nitem = 0, last_link = -1;
     int s = 0, n = 0;  // slot and round of stage gstage (gstage = n*S + s), kept without division
@@ -255,6 +264,14 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
       // previous kernel in the stream has completed; links do not depend on it
       if (nitem == 0) ptx::wait_dependencies();
       const PsiT* base_t = static_cast<const PsiT*>(J.j[job].in) + (size_t)p.t * NC * V3;
+      // Whole-plane tiles stage planes z-1, z, z+1 as rows 0..3k-1; where the
+      // three planes are consecutive in memory one copy per colour moves them.
+      // Halo tiles: rows y0-1 .. y0+k of plane z in one run unless the y halo
+      // wraps (then two), rows y0 .. y0+k-1 of planes z-1 and z+1 one each.
+      const bool ywrap_lo = p.y0 == 0, ywrap_hi = p.y0 + k == Ly;
+      int npieces = ywrap_lo || ywrap_hi ? 4 : 3;
+      if (!halo) npieces = Lz < 3 ? 3 : (p.z == 0 || p.z == Lz - 1 ? 2 : 1);
+      const int ncopies = G * 3 * npieces;
       for (int j = 0; j < SPI; ++j, ++gstage, s = s + 1 == S ? 0 : s + 1, n += s == 0) {
         if (n > 0) {
           const bool ok = ptx::mbar_wait_bounded(empty0 + 8 * s, (n - 1) & 1, timeout_ns);
@@ -267,29 +284,55 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
         if (gstage == drop_stage) continue;  // test hook: the waits for this stage run out
         if (lane == 0) ptx::mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
         __syncwarp();
+        if (tt.use_tmap && npieces == 1) {
+          // one box: x, rows of planes z-1..z+1, the stage's G vectors, 3 colours
+          const int v = p.part * VPI + j * G;
+          if (lane == 0)
+            ptx::tensor_g2s_4d(ptx::smem_addr(st + (size_t)s * stage_elems), &J.tmap[job], 0, zm * Ly, v % COLS,
+                               3 * (v / COLS) + COLS * p.t, full0 + 8 * s);
+          continue;
+        }
         for (int cp = lane; cp < ncopies; cp += 32) {
           const int gg = cp / (3 * npieces), rem = cp % (3 * npieces);
           const int c = rem / npieces, piece = rem % npieces;
           int src_off, dst_row, nrows;
           if (halo) {
-            switch (piece) {
-              case 0: src_off = (p.z * Ly + ym) * Lx; dst_row = 0; nrows = 1; break;
-              case 1: src_off = (p.z * Ly + p.y0) * Lx; dst_row = 1; nrows = k; break;
-              case 2: src_off = (p.z * Ly + yp) * Lx; dst_row = k + 1; nrows = 1; break;
-              case 3: src_off = (zm * Ly + p.y0) * Lx; dst_row = rowsA; nrows = k; break;
-              default: src_off = (zp * Ly + p.y0) * Lx; dst_row = rowsA + k; nrows = k; break;
+            const int pz = npieces == 3 ? piece + 1 : piece;  // 0, 1: plane z in two runs; 1 alone: one run
+            if (pz == 0) {  // the run before the wrap
+              src_off = (p.z * Ly + ym) * Lx; dst_row = 0; nrows = ywrap_lo ? 1 : k + 1;
+            } else if (pz == 1) {
+              if (npieces == 3) {
+                src_off = (p.z * Ly + ym) * Lx; dst_row = 0; nrows = k + 2;
+              } else if (ywrap_lo) {
+                src_off = (p.z * Ly + p.y0) * Lx; dst_row = 1; nrows = k + 1;
+              } else {
+                src_off = (p.z * Ly + yp) * Lx; dst_row = k + 1; nrows = 1;
+              }
+            } else if (pz == 2) {
+              src_off = (zm * Ly + p.y0) * Lx; dst_row = rowsA; nrows = k;
+            } else {
+              src_off = (zp * Ly + p.y0) * Lx; dst_row = rowsA + k; nrows = k;
+            }
+          } else if (npieces == 1) {  // planes z-1, z, z+1 in one run
+            src_off = zm * Ly * Lx; dst_row = 0; nrows = 3 * k;
+          } else if (npieces == 2) {  // z = 0: z-1 wraps; z = Lz-1: z+1 wraps
+            const bool first = piece == 0;
+            if (p.z == 0) {
+              src_off = (first ? zm : p.z) * Ly * Lx; dst_row = first ? 0 : k; nrows = first ? k : 2 * k;
+            } else {
+              src_off = (first ? zm : zp) * Ly * Lx; dst_row = first ? 0 : 2 * k; nrows = first ? 2 * k : k;
             }
           } else {
             switch (piece) {
-              case 0: src_off = (p.z * Ly + p.y0) * Lx; dst_row = 0; nrows = k; break;
-              case 1: src_off = (zm * Ly + p.y0) * Lx; dst_row = rowsA; nrows = k; break;
-              default: src_off = (zp * Ly + p.y0) * Lx; dst_row = rowsA + k; nrows = k; break;
+              case 0: src_off = zm * Ly * Lx; dst_row = 0; nrows = k; break;
+              case 1: src_off = p.z * Ly * Lx; dst_row = k; nrows = k; break;
+              default: src_off = zp * Ly * Lx; dst_row = 2 * k; nrows = k; break;
             }
           }
           const int v = p.part * VPI + j * G + gg;
           const int comp = (v / COLS) * 3 * COLS + c * COLS + (v % COLS);
           const PsiT* src = base_t + (size_t)comp * V3 + src_off;
-          const uint32_t dst = ptx::smem_addr(st + (size_t)s * stage_elems + (gg * 3 + c) * CS + dst_row * Lx);
+          const uint32_t dst = ptx::smem_addr(st + (size_t)s * stage_elems + (c * G + gg) * CS + dst_row * Lx);
           ptx::bulk_g2s(dst, src, (uint32_t)(nrows * Lx) * sizeof(PsiT), full0 + 8 * s);
         }
       }
@@ -311,13 +354,15 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
   const int r = active ? ctid / Lx : 0;
   const int x = active ? ctid % Lx : 0;
   const int xm = x == 0 ? Lx - 1 : x - 1;
-  // shared-memory offsets (elements, within a colour region) of the seven sites
-  const int rc = r + halo;
+  // shared-memory offsets (elements, within a colour region) of the seven
+  // sites; rows of plane z from bz, of planes z-1 and z+1 from bzm and bzp
+  const int bz = halo ? 0 : k, bzm = halo ? rowsA : 0, bzp = halo ? rowsA + k : 2 * k;
+  const int rc = bz + r + halo;
   const int oc = rc * Lx + x;
-  const int yp_row = halo ? r + 2 : (r + 1 == k ? 0 : r + 1);
-  const int ym_row = halo ? r : (r == 0 ? k - 1 : r - 1);
-  const int of[3] = {rc * Lx + (x + 1 == Lx ? 0 : x + 1), yp_row * Lx + x, (rowsA + k + r) * Lx + x};
-  const int ob[3] = {rc * Lx + xm, ym_row * Lx + x, (rowsA + r) * Lx + x};
+  const int yp_row = bz + (halo ? r + 2 : (r + 1 == k ? 0 : r + 1));
+  const int ym_row = bz + (halo ? r : (r == 0 ? k - 1 : r - 1));
+  const int of[3] = {rc * Lx + (x + 1 == Lx ? 0 : x + 1), yp_row * Lx + x, (bzp + r) * Lx + x};
+  const int ob[3] = {rc * Lx + xm, ym_row * Lx + x, (bzm + r) * Lx + x};
   // link-buffer offsets of this site's six links
   const int lf = r * Lx + x;
   const bool yh = halo && r == 0;
@@ -363,18 +408,18 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
         PsiT* po = outp + (size_t)((v0 / COLS) * 3 * COLS + (v0 % COLS)) * V3;
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
-          const PsiT* sg = sp + gg * 3 * CS;
+          const PsiT* sg = sp + gg * CS;  // colour q of vector gg: region q * G + gg
           u64 nf[3][3], nb[3][3];
           float2 c[3], o[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              nf[i][q] = lds_pair(sg + of[i] + q * CS);
-              nb[i][q] = lds_pair(sg + ob[i] + q * CS);
+              nf[i][q] = lds_pair(sg + of[i] + q * G * CS);
+              nb[i][q] = lds_pair(sg + ob[i] + q * G * CS);
             }
 #pragma unroll
-          for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * CS);
+          for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * G * CS);
           hop_vector(L, nf, nb, c, kappa, o);
 #pragma unroll
           for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);

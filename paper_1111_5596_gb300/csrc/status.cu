@@ -20,6 +20,7 @@ int g_tile_consumers = 0;  // 0: the library's default for the geometry
 int g_tile_stages = 0;
 int g_tile_grid = 0;
 int g_f16_warps = 0;  // 0: the library's default (16)
+int g_tensor_copy_off = 0;  // 1: the pipelined hop stages with bulk copies only
 
 }  // namespace
 
@@ -42,6 +43,7 @@ int debug_tile_consumers() { return g_tile_consumers; }
 int debug_tile_stages() { return g_tile_stages; }
 int debug_tile_grid() { return g_tile_grid; }
 int debug_f16_warps() { return g_f16_warps; }
+int debug_tensor_copy_off() { return g_tensor_copy_off; }
 
 }  // namespace qdpg
 
@@ -92,6 +94,10 @@ int qdpg_debug_set(int what, long long value) {
     case QDPG_TUNE_F16_WARPS:
       if (value != 0 && value != 8 && value != 16) return fail(QDPG_ERR_ARG, "debug_set: f16 consumer warps must be 8 or 16");
       g_f16_warps = (int)value;
+      return ok();
+    case QDPG_TUNE_TENSOR_COPY:
+      if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: tensor-copy setting outside 0..1");
+      g_tensor_copy_off = (int)value;
       return ok();
     case QDPG_TUNE_GRID:
       if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: grid mode outside 0..1");

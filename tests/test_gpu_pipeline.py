@@ -18,10 +18,13 @@ def _field(q, lat, kind, prec, canon):
 @pytest.mark.parametrize("dims,prec,sites", [((16, 16, 16, 4), "f32", 0), ((8, 12, 6, 3), "f32", 0),
                                              ((24, 24, 8, 2), "f32", 0), ((24, 24, 4, 2), "f32", 288),
                                              ((48, 12, 3, 2), "bf16", 288), ((8, 8, 8, 4), "bf16", 0),
-                                             ((12, 6, 4, 2), "bf16", 0)])
+                                             ((12, 6, 4, 2), "bf16", 0), ((16, 16, 2, 3), "f32", 0),
+                                             ((16, 8, 1, 2), "f32", 0), ((16, 16, 3, 2), "bf16", 0)])
 def test_pipelined_equals_simple_kernel(qdpg_gpu, dims, prec, sites):
     """sites: most sites per tile (0 = default); 288 gives 12-row tiles at
-    Lx = 24 and 6-row tiles at Lx = 48."""
+    Lx = 24 and 6-row tiles at Lx = 48.  Whole-plane tiles with Lz = 1, 2, 3
+    cover the staging of planes z-1, z, z+1 in one, two or three copies;
+    halo tiles at the first, last and inner rows cover the y-halo runs."""
     q = qdpg_gpu
     q.debug_set(q.TUNE_TILE_CONSUMERS, sites)
     try:
