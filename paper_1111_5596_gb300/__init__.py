@@ -120,7 +120,7 @@ def launch_count() -> int:
 
 
 DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_STAGE, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
-TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_GRID = 4, 5, 7
+TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_GRID, TUNE_TENSOR_COPY = 4, 5, 7, 9
 
 
 def device_status(stream=None):

@@ -241,18 +241,32 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
         }
         if (lane == 0) ptx::mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
         __syncwarp();
-        if (lane < npieces) {
-          int src_row, dst_row, nrows;
-          const int z2 = (halo ? (lane < 3) : (lane == 0)) ? p.z : ((halo ? lane == 3 : lane == 1) ? zm : zp);
+        // rows y0-1 .. y0+k of plane z in one run unless the y halo wraps
+        // (then two), rows y0 .. y0+k-1 of planes z-1 and z+1 one each
+        const bool wlo = p.y0 == 0, whi = p.y0 + k == Ly;
+        const int np = halo ? (wlo || whi ? 4 : 3) : npieces;
+        if (lane < np) {
+          int z2, src_row, dst_row, nrows;
           if (halo) {
-            switch (lane) {
-              case 0: src_row = ym; dst_row = 0; nrows = 1; break;
-              case 1: src_row = p.y0; dst_row = 1; nrows = k; break;
-              case 2: src_row = yp; dst_row = k + 1; nrows = 1; break;
-              case 3: src_row = p.y0; dst_row = rowsA; nrows = k; break;
-              default: src_row = p.y0; dst_row = rowsA + k; nrows = k; break;
+            const int pz = np == 3 ? lane + 1 : lane;  // 0, 1: plane z (1 alone: one run); 2: z-1; 3: z+1
+            if (pz == 0) {
+              z2 = p.z; src_row = ym; dst_row = 0; nrows = wlo ? 1 : k + 1;
+            } else if (pz == 1) {
+              z2 = p.z;
+              if (np == 3) {
+                src_row = ym; dst_row = 0; nrows = k + 2;
+              } else if (wlo) {
+                src_row = p.y0; dst_row = 1; nrows = k + 1;
+              } else {
+                src_row = yp; dst_row = k + 1; nrows = 1;
+              }
+            } else if (pz == 2) {
+              z2 = zm; src_row = p.y0; dst_row = rowsA; nrows = k;
+            } else {
+              z2 = zp; src_row = p.y0; dst_row = rowsA + k; nrows = k;
             }
           } else {
+            z2 = lane == 0 ? p.z : (lane == 1 ? zm : zp);
             src_row = p.y0;
             nrows = k;
             dst_row = lane == 0 ? 0 : (lane == 1 ? rowsA : rowsA + k);

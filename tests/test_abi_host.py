@@ -221,3 +221,22 @@ def test_batch_planning_validates_jobs_on_host(q):
     assert L.qdpg_batch_run(None, 0, None) == ERR_ARG
     L.qdpg_batch_destroy(None)
     assert q.launch_count() == launches_before
+
+
+def test_tuning_settings_are_validated_on_host(q):
+    """Launch-shape settings of the smearing kernels: accepted within their
+    ranges, rejected outside them, and reset to the defaults."""
+    L = q._lib
+    TILE, STAGES, F16_WARPS, TENSOR_COPY = 4, 5, 8, 9
+    try:
+        assert L.qdpg_debug_set(TILE, 288) == OK                # 12-row tiles at Lx = 24
+        assert L.qdpg_debug_set(TILE, 289) == ERR_ARG
+        assert L.qdpg_debug_set(TILE, 16) == ERR_ARG
+        assert L.qdpg_debug_set(STAGES, 17) == ERR_ARG
+        assert L.qdpg_debug_set(F16_WARPS, 12) == ERR_ARG
+        assert L.qdpg_debug_set(TENSOR_COPY, 1) == OK           # bulk copies only
+        assert L.qdpg_debug_set(TENSOR_COPY, 2) == ERR_ARG
+        assert L.qdpg_debug_set(99, 0) == ERR_ARG               # unknown setting
+    finally:
+        for what in (TILE, STAGES, F16_WARPS, TENSOR_COPY):
+            assert L.qdpg_debug_set(what, 0) == OK

@@ -102,3 +102,29 @@ def test_autotuner_picks_a_config_and_keeps_parity(qdpg_gpu, tmp_path):
     q.tune_load(path)
     text = open(path).read()
     assert f"16 16 8 2 3 {q.F32} {q.F32} {sites} {grid_mode}" in text
+
+
+@pytest.mark.parametrize("prec", ["f32", "bf16"])
+def test_tensor_map_and_bulk_staging_agree(qdpg_gpu, prec):
+    """Whole-plane tiles stage interior planes with one tensor-map copy per
+    stage; the bulk-copy staging of the same rows gives the same bits."""
+    q = qdpg_gpu
+    dims = (16, 16, 6, 2)
+    lat = q.Lattice(dims, 3)
+    U = fields.round_to_f32(fields.gauge_field(dims, 37, kind="haar"))
+    psi = fields.round_to_f32(fields.propagator(dims, 37, envelope=0.3))
+    p = q.PREC_NAMES[prec]
+    Uf = _field(q, lat, q.GAUGE, q.F32, U)
+    outs = []
+    for off in (0, 1):
+        q.debug_set(q.TUNE_TENSOR_COPY, off)
+        try:
+            f = _field(q, lat, q.PROPAGATOR, p, psi)
+            q.gauss_smear(Uf, f, 0.2, 4, scratch=f.like())
+            q.device_status()
+            outs.append(f.export().cpu().numpy())
+        finally:
+            q.debug_set(q.TUNE_TENSOR_COPY, 0)
+    assert np.array_equal(outs[0], outs[1])
+    if prec == "f32":
+        assert field_err(outs[0], smear.gauss_smear(U, psi, 0.2, 4)) <= TOL_F32
