@@ -283,13 +283,14 @@ def batch_arms(q, dev, args) -> dict:
         r = {"job": j, "lat": lat, "P": P_can,
              "U32": q.Field(lat, q.GAUGE, q.F32, device=dev).import_(U_can),
              "Ub": q.Field(lat, q.GAUGE, q.BF16_R12, device=dev).import_(U_can),
-             "Uh": q.Field(lat, q.GAUGE, q.F16_R12, device=dev).import_(U_can)}
+             "Uh": q.Field(lat, q.GAUGE, q.F16_R12, device=dev).import_(U_can),
+             "Uf": q.Field(lat, q.GAUGE, q.F16, device=dev).import_(U_can)}
         del U_can
-        for tag, prec in (("32", q.F32), ("b", q.BF16), ("h", q.F16)):
+        for tag, prec in (("32", q.F32), ("b", q.BF16), ("h", q.F16), ("f", q.F16)):
             r["p" + tag] = q.Field(lat, q.PROPAGATOR, prec, device=dev)
             r["s" + tag] = r["p" + tag].like()
         r["m1"] = torch.zeros((16, 1, lat.Nt), dtype=torch.complex128, device=dev)
-        for tag in ("32", "b", "h"):
+        for tag in ("32", "b", "h", "f"):
             r["m" + tag] = torch.zeros((16, lat.Nt), dtype=torch.complex128, device=dev)
         rows.append(r)
     # launch shapes per (lattice, precision) class, by the autotuner
@@ -304,6 +305,7 @@ def batch_arms(q, dev, args) -> dict:
     b32 = q.Batch([(r["U32"], r["p32"], r["s32"], r["job"]["kappa"], r["job"]["n_iter"], r["m32"]) for r in rows])
     bb = q.Batch([(r["Ub"], r["pb"], r["sb"], r["job"]["kappa"], r["job"]["n_iter"], r["mb"]) for r in rows])
     bh = q.Batch([(r["Uh"], r["ph"], r["sh"], r["job"]["kappa"], r["job"]["n_iter"], r["mh"]) for r in rows])
+    bf = q.Batch([(r["Uf"], r["pf"], r["sf"], r["job"]["kappa"], r["job"]["n_iter"], r["mf"]) for r in rows])
 
     def single_fp32():
         for r in rows:
@@ -334,6 +336,7 @@ def batch_arms(q, dev, args) -> dict:
     t_b32 = timed(lambda: batched(b32, "32"))
     t_bb = timed(lambda: batched(bb, "b"))
     t_bh = timed(lambda: batched(bh, "h"))
+    t_bf = timed(lambda: batched(bf, "f"))
 
     # correlator error of the BF16 batch against FP32, per job: max over
     # channels of ||C_bf16(.) - C_f32(.)|| / ||C_f32(.)|| over t
@@ -345,6 +348,7 @@ def batch_arms(q, dev, args) -> dict:
 
     errs = [corr_err(r["mb"], r["m32"]) for r in rows]
     errs_h = [corr_err(r["mh"], r["m32"]) for r in rows]
+    errs_f = [corr_err(r["mf"], r["m32"]) for r in rows]
     # FP32 one at a time and FP32 batched run the same per-site arithmetic:
     # the smeared fields agree bit for bit (the correlators only to the
     # order of their FP64 atomic timeslice sums)
@@ -380,6 +384,9 @@ def batch_arms(q, dev, args) -> dict:
         "speedup_f16_tc_batched_vs_fp32_single": t_single / t_bh,
         "f16_vs_fp32_corr_rel_err_max": max(errs_h), "f16_vs_fp32_corr_rel_err_max_by_n": by_n_h,
         "f16_tol": 2e-2, "f16_within_tol": max(errs_h) <= 2e-2,
+        "f16_full_links": {"ms_per_pass": t_bf, "speedup_vs_fp32_single": t_single / t_bf,
+                           "corr_rel_err_max": max(errs_f), "within_tol": max(errs_f) <= 2e-2,
+                           "storage": "propagators float16 x scale, links float16 (all nine entries)"},
         "f16_storage": "propagators float16 x per-field power-of-two scale, links float16 reconstruct-12, "
                        "tensor-core hop (mma.sync m16n8k16, FP32 accumulation)",
         "speedup_bf16_batched_vs_fp32_single": t_single / t_bb,
