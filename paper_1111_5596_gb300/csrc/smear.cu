@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kSmearThreads) smear_hop_kernel(const PsiT* __
   }
   const long long p0 = (long long)t * NC * V3 + s3;
   SiteLinks L;
-  make_site_links(Uf, Ub, L);
+  make_site_links(Uf, Ub, kappa, L);
 
 #pragma unroll 1
   for (int v = 0; v < 4 * COLS; ++v) {
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kSmearThreads) smear_hop_kernel(const PsiT* __
       }
 #pragma unroll
     for (int a = 0; a < 3; ++a) c[a] = ld2(in + p0 + (long long)(cb + a * COLS) * V3);
-    hop_vector(L, nf, nb, c, kappa, o);
+    hop_vector(L, nf, nb, c, o);
 #pragma unroll
     for (int a = 0; a < 3; ++a) st2(out + p0 + (long long)(cb + a * COLS) * V3, o[a]);
   }

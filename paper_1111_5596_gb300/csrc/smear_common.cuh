@@ -90,30 +90,31 @@ __device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
   return d;
 }
 
-// Links of one site as pairs: f[i][a*3+q] = U_i(x)[a][q] and
-// b[i][a*3+q] = conj(U_i(x - i)[q][a]) (the backward hop's matrix).
+// Links of one site as pairs, multiplied by kappa once per site:
+// f[i][a*3+q] = kappa U_i(x)[a][q] and b[i][a*3+q] = kappa conj(U_i(x - i)[q][a])
+// (the backward hop's matrix).
 struct SiteLinks {
   u64 f[3][9];
   u64 b[3][9];
 };
 
-__device__ __forceinline__ void make_site_links(const float2 Uf[3][9], const float2 Ub[3][9], SiteLinks& L) {
+__device__ __forceinline__ void make_site_links(const float2 Uf[3][9], const float2 Ub[3][9], float kappa,
+                                                SiteLinks& L) {
 #pragma unroll
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int a = 0; a < 3; ++a)
 #pragma unroll
       for (int q = 0; q < 3; ++q) {
-        L.f[i][a * 3 + q] = pack2(Uf[i][a * 3 + q]);
-        L.b[i][a * 3 + q] = pack2(Ub[i][q * 3 + a].x, -Ub[i][q * 3 + a].y);
+        L.f[i][a * 3 + q] = pack2(kappa * Uf[i][a * 3 + q].x, kappa * Uf[i][a * 3 + q].y);
+        L.b[i][a * 3 + q] = pack2(kappa * Ub[i][q * 3 + a].x, -(kappa * Ub[i][q * 3 + a].y));
       }
 }
 
-// Half a hop for one colour vector: with M[i] = the site's forward links
-// U_i(x) (or its conjugated backward links conj(U_i(x-i))^T) and n[i][q] the
-// matching neighbour values, h[a] = sum_i (M[i] n[i])[a] as (re, im).
-__device__ __forceinline__ void hop_half(const u64 M[3][9], const u64 n[3][3], float2 h[3]) {
-  u64 P[3] = {0ull, 0ull, 0ull}, Q[3] = {0ull, 0ull, 0ull};
+// Products of one half of the hop (M = the forward or the conjugated
+// backward links, n[i][q] the matching neighbour values) accumulated into
+// the pairs P[a] (real part P.x - P.y) and Q[a] (imaginary part Q.x + Q.y).
+__device__ __forceinline__ void hop_accumulate(const u64 M[3][9], const u64 n[3][3], u64 P[3], u64 Q[3]) {
 #pragma unroll
   for (int i = 0; i < 3; ++i) {
     u64 sw[3];
@@ -127,29 +128,29 @@ __device__ __forceinline__ void hop_half(const u64 M[3][9], const u64 n[3][3], f
         Q[a] = fma2(M[i][a * 3 + q], sw[q], Q[a]);
       }
   }
+}
+
+// One colour vector of one site: out[a] = c[a] + sum_i
+//   [ kappa U_i(x) psi(x+i) + (kappa U_i(x-i))^dag psi(x-i) ][a]
+// from neighbour values nf[i][q] = psi(x+i)[q], nb[i][q] = psi(x-i)[q] and
+// kappa-scaled links.  The centre value seeds the accumulators (P = (c.x, 0),
+// Q = (0, c.y)); forward products go in first, then backward ones.  Every
+// kernel uses this sequence, so their results agree bit for bit.
+__device__ __forceinline__ void hop_vector(const SiteLinks& L, const u64 nf[3][3], const u64 nb[3][3],
+                                           const float2 c[3], float2 out[3]) {
+  u64 P[3], Q[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    P[a] = pack2(c[a].x, 0.f);
+    Q[a] = pack2(0.f, c[a].y);
+  }
+  hop_accumulate(L.f, nf, P, Q);
+  hop_accumulate(L.b, nb, P, Q);
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
     const float2 p = unpack2(P[a]), qv = unpack2(Q[a]);
-    h[a] = make_float2(p.x - p.y, qv.x + qv.y);
+    out[a] = make_float2(p.x - p.y, qv.x + qv.y);
   }
-}
-
-// out[a] = c[a] + kappa * (forward half + backward half)[a]; every kernel
-// combines the two halves in this order, so their results agree bit for bit.
-__device__ __forceinline__ float2 hop_combine(float2 c, float2 hf, float2 hb, float kappa) {
-  return make_float2(fmaf(kappa, hf.x + hb.x, c.x), fmaf(kappa, hf.y + hb.y, c.y));
-}
-
-// One colour vector of one site: out[a] = c[a] + kappa * sum_i
-//   [ U_i(x) psi(x+i) + U_i(x-i)^dag psi(x-i) ][a]
-// from neighbour values nf[i][q] = psi(x+i)[q], nb[i][q] = psi(x-i)[q].
-__device__ __forceinline__ void hop_vector(const SiteLinks& L, const u64 nf[3][3], const u64 nb[3][3],
-                                           const float2 c[3], float kappa, float2 out[3]) {
-  float2 hf[3], hb[3];
-  hop_half(L.f, nf, hf);
-  hop_half(L.b, nb, hb);
-#pragma unroll
-  for (int a = 0; a < 3; ++a) out[a] = hop_combine(c[a], hf[a], hb[a], kappa);
 }
 
 }  // namespace smear_dev

@@ -388,7 +388,7 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
       link_from_smem<LMODE>(lbuf + r * Lx + xm, kLx, Ub[0]);
       link_from_smem<LMODE>(lbuf + lyb, lyb_stride, Ub[1]);
       link_from_smem<LMODE>(lbuf + lk_ZB + lf, kLx, Ub[2]);
-      make_site_links(Uf, Ub, L);
+      make_site_links(Uf, Ub, kappa, L);
     }
     __syncwarp();
     if (lane == 0) ptx::mbar_arrive(lempty);
@@ -420,7 +420,7 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
             }
 #pragma unroll
           for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * G * CS);
-          hop_vector(L, nf, nb, c, kappa, o);
+          hop_vector(L, nf, nb, c, o);
 #pragma unroll
           for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);
         }
