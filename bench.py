@@ -68,6 +68,7 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the 64-job batched comparison (FP32 one job at a time vs batched FP32/BF16)")
     ap.add_argument("--batch-steps", type=int, default=5)
+    ap.add_argument("--no-24x48", action="store_true", help="skip the 24^3x48 smearing-hop roofline component")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the 48^3x96 scale run (8 propagators, 64 meson pairs + nucleon at 33 momenta)")
     return ap.parse_args()
@@ -125,19 +126,63 @@ def checker_inputs(w, t0: int, t1: int):
     return U, P
 
 
+def _checker_timeslice(args):
+    """One timeslice of the step through the FP64 checker (a pool task)."""
+    w, t, Ut, Pt = args
+    run_checker_sample(w, 0, Ut, Pt)
+    return t
+
+
+def checker_pool(n: int):
+    """A spawned process pool of n workers, one numpy thread each (a child
+    forked from a process that has initialised CUDA can hang)."""
+    import multiprocessing as mp
+
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    return mp.get_context("spawn").Pool(n)
+
+
+def host_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def checker_timed(w, pool, n_workers: int, n_timeslices: int):
+    """Wall time of n_timeslices whole timeslices of the step through the
+    checker, spread over the pool (smearing and contractions never couple
+    timeslices, so each timeslice is an exact, independent share)."""
+    U, P = checker_inputs(w, 0, n_timeslices)
+    tasks = [(w, t, U[:, t:t + 1], P[t:t + 1]) for t in range(n_timeslices)]
+    t0 = time.perf_counter()
+    done = pool.map(_checker_timeslice, tasks, chunksize=1)
+    dt = time.perf_counter() - t0
+    assert sorted(done) == list(range(n_timeslices))
+    return dt
+
+
 def cpu_baseline(w, min_seconds: float) -> dict:
-    """Time the checker on whole timeslices until min_seconds of host time."""
-    U, P = checker_inputs(w, 0, 4)
-    done, t_total = 0, 0.0
-    while done < 4 and (t_total < min_seconds or done == 0):
-        t0 = time.perf_counter()
-        run_checker_sample(w, done, U, P)
-        t_total += time.perf_counter() - t0
-        done += 1
-    b = step_bytes(w, n_timeslices=done)["total"]
-    return {"value": b / t_total / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": f"{done} of {w.Nt} timeslices of the step (SRC + SNK smearing N={w.n_smear}, "
-                      f"16 mesons), numpy FP64, {t_total:.1f} s"}
+    """The checker on the host cores over whole timeslices of the step: one
+    timeslice per worker and round, the whole lattice when it fits the time
+    (min_seconds of wall time is the floor of the sample)."""
+    cores = min(host_cores(), w.Nt)
+    pool = checker_pool(cores)
+    try:
+        pool.map(_checker_timeslice, [(w, 0) + checker_inputs(w, 0, 1)] * cores, chunksize=1)  # warm the workers
+        n = cores
+        dt = checker_timed(w, pool, cores, n)
+        if dt < min_seconds and n < w.Nt:
+            n = w.Nt
+            dt = checker_timed(w, pool, cores, n)
+    finally:
+        pool.terminate()
+        pool.join()
+    b = step_bytes(w, n_timeslices=n)["total"]
+    return {"value": b / dt / 1e9, "unit": "GB/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} of {w.Nt} timeslices of the step (SRC + SNK smearing N={w.n_smear}, 16 mesons), "
+                      f"numpy FP64, one timeslice per process on {cores} host cores, {dt:.1f} s wall"}
 
 
 def reference_arm(args):
@@ -145,23 +190,26 @@ def reference_arm(args):
     if rank != 0:
         return
     w = workload()
-    U, P = checker_inputs(w, 0, 1)
-    for _ in range(args.warmup):
-        run_checker_sample(w, 0, U, P)
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        run_checker_sample(w, 0, U, P)
-    dt = (time.perf_counter() - t0) / args.steps
-    b = step_bytes(w, n_timeslices=1)["total"]
+    cores = min(host_cores(), w.Nt)
+    pool = checker_pool(cores)
+    try:
+        for _ in range(args.warmup):
+            checker_timed(w, pool, cores, cores)
+        dts = [checker_timed(w, pool, cores, cores) for _ in range(args.steps)]
+    finally:
+        pool.terminate()
+        pool.join()
+    dt = sum(dts) / len(dts)
+    b = step_bytes(w, n_timeslices=cores)["total"]
     value = b / dt / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_block(w),
-        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": 1, "kind": "oracle",
-                         "sample": f"1 of {w.Nt} timeslices per step (SRC + SNK smearing N={w.n_smear}, "
-                                   f"16 mesons), numpy FP64"},
+        "cpu_baseline": {"value": value, "unit": "GB/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{cores} of {w.Nt} timeslices per step (SRC + SNK smearing N={w.n_smear}, "
+                                   f"16 mesons), numpy FP64, one timeslice per process on {cores} host cores"},
         "e2e": {"value": value, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -446,8 +494,8 @@ def scale_run(q, dev, args) -> dict:
         for i, (kappa, n) in enumerate(kn):
             P_can = synth_dev.propagator(w.dims, w.seed + 17 * i, dev)
             f = q.Field(lat, q.PROPAGATOR, pp, device=dev).import_(P_can)
-            if arm == "fp32" and i == 0:
-                sample["P"] = P_can[:1].cpu().numpy()
+            if arm == "fp32" and i in (IA, IB):
+                sample[i] = P_can[:1].cpu().numpy()
             del P_can
             torch.cuda.synchronize()
             e0, e1 = ev(), ev()
@@ -490,24 +538,100 @@ def scale_run(q, dev, args) -> dict:
                                                     for a in range(len(kn)) for b in range(len(kn)))
     res["f16_vs_fp32_nucleon_corr_rel_err"] = corr_err(N16, N32)
     res["f16_tol"] = 2e-2
-    # FP32 against the checker: propagator 0 ((0.15, 10)) on timeslice 0, all 16 mesons at 33 momenta
+    # FP32 against the checker: the cross pair of the (0.30, 80) propagator
+    # (rescaled by the scale records) and a (0.15, 10) one on timeslice 0, all
+    # 16 mesons at 33 momenta; the checker's 24 source columns (each smears
+    # alone: the operator acts on colour) are spread over the host cores
     t0 = time.perf_counter()
-    kappa0, n0 = kn[0]
-    S = smear.gauss_smear(sample["U"].astype(np.complex128), sample["P"].astype(np.complex128), kappa0, n0,
-                          w.j_decay)
-    ref = hadron.meson_2pt(S, S, hadron.SIXTEEN_MESONS, moms, j_decay=w.j_decay)
+    (ka, na), (kb, nb) = kn[IA], kn[IB]
+    U0 = sample["U"].astype(np.complex128)
+    cores = host_cores()
+    pool = checker_pool(min(cores, 24))
+    try:
+        cols = [pool.apply_async(_smear_column, (U0, np.ascontiguousarray(sample[i][..., sp, cp]).astype(np.complex128),
+                                                 kk, nn))
+                for i, kk, nn in ((IA, ka, na), (IB, kb, nb)) for sp in range(4) for cp in range(3)]
+        got_cols = [c.get() for c in cols]
+    finally:
+        pool.terminate()
+        pool.join()
+    Sa = np.stack(got_cols[:12], axis=-1).reshape(got_cols[0].shape + (4, 3))
+    Sb = np.stack(got_cols[12:], axis=-1).reshape(got_cols[0].shape + (4, 3))
+    ref = hadron.meson_2pt(Sa, Sb, hadron.SIXTEEN_MESONS, moms, j_decay=w.j_decay)
     # scale of each momentum sum: A(t) = sum_x |c(x)| (a smooth field's p != 0
     # correlators cancel strongly; FP32 site values bound the error relative to A)
-    A = np.stack([np.abs(hadron.meson_site(S, S, a, b)).sum(axis=(1, 2, 3)) for a, b in hadron.SIXTEEN_MESONS])
-    got = C32[0, 0][:, :, :1]
+    A = np.stack([np.abs(hadron.meson_site(Sa, Sb, a, b)).sum(axis=(1, 2, 3)) for a, b in hadron.SIXTEEN_MESONS])
+    got = C32[IA, IB][:, :, :1]
     k0 = moms.index((0, 0, 0))
     res["fp32_vs_checker"] = {
-        "sample": "propagator 0 (kappa 0.15, N 10), timeslice 0, 16 mesons x 33 momenta",
+        "sample": f"cross pair S_a S_b, a = propagator {IA} (kappa {ka}, N {na}, rescaled by the scale record), "
+                  f"b = propagator {IB} (kappa {kb}, N {nb}), timeslice 0, 16 mesons x 33 momenta",
         "p0_corr_rel_err": corr_err(got[:, k0:k0 + 1], ref[:, k0:k0 + 1]),
         "err_rel_to_abs_site_sum": float((np.abs(got - ref)[..., 0] / A).max()),
         "plain_corr_rel_err_all_p": corr_err(got, ref), "tol": 1e-5,
-        "checker_s": time.perf_counter() - t0}
+        "largest_smeared_value_log2": float(np.log2(np.abs(Sa).max())),
+        "checker_s": time.perf_counter() - t0, "checker_cores": min(cores, 24)}
     return res
+
+
+def _smear_column(U, col, kappa, n_iter):
+    """One source column of a propagator timeslice through the FP64 checker (a pool task)."""
+    from oracle import smear
+
+    return smear.gauss_smear(U, col, kappa, n_iter, 3)
+
+
+IA, IB = 6, 1   # the scale workload's propagators at (0.30, 80) and (0.15, 10)
+
+
+def hop_24x48(q, dev, args) -> dict:
+    """The smearing hop on the 24^3x48 lattice (the shape of the paper's run B,
+    Fig. 4b), FP32 propagator and links, kappa = 0.21, in the tuned launch
+    shape: mean per-launch time from CUDA events around each launch, and back
+    to back (events around whole smearing calls), as a roofline block."""
+    import torch
+
+    from synth import configs, device as synth_dev
+
+    w = configs.BF16_24x48
+    lat = q.Lattice(w.dims, w.j_decay)
+    U = q.Field(lat, q.GAUGE, q.F32, device=dev).import_(
+        synth_dev.gauge_field(w.dims, w.seed, dev, kind=w.links, eps=w.eps))
+    S = q.Field(lat, q.PROPAGATOR, q.F32, device=dev).import_(synth_dev.propagator(w.dims, w.seed, dev))
+    scratch = S.like()
+    tuned = (None, None, None) if args.no_tune else q.tune_smear(U, S, scratch, w.j_decay, reps=3)
+    n_b2b = 26          # below the rescaling threshold at kappa = 0.21 (40 bits): hops only
+    for _ in range(2):
+        q.gauss_smear(U, S, w.kappa, n_b2b, w.j_decay, scratch=scratch)
+    torch.cuda.synchronize()
+    q.profile_reset()
+    q.profile_enable(True)
+    for _ in range(2):
+        q.gauss_smear(U, S, w.kappa, n_b2b, w.j_decay, scratch=scratch)
+    torch.cuda.synchronize()
+    q.profile_enable(False)
+    hop_ms, hop_n = q.profile_query("smear_hop")
+    stream = torch.cuda.current_stream()
+    ev = []
+    for _ in range(3):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        q.gauss_smear(U, S, w.kappa, n_b2b, w.j_decay, scratch=scratch)
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    q.device_status()
+    b2b_s = min(a.elapsed_time(z) for a, z in ev) * 1e-3 / n_b2b
+    avg_s = hop_ms * 1e-3 / hop_n
+    per_launch = lat.V * (2 * 1152 + 216)
+    peak = measured_peaks()
+    return {"kernel": "smear_hop (FP32 propagator, 12 columns)", "lattice": "24x24x24x48", "bound": "hbm",
+            "achieved": per_launch / avg_s / 1e9, "peak": peak["hbm_gbs"], "unit": "GB/s",
+            "frac": per_launch / avg_s / 1e9 / peak["hbm_gbs"], "peak_source": peak["source"],
+            "traffic": traffic_for("smear_hop_24x48"), "algorithmic_bytes_per_launch": per_launch,
+            "avg_launch_us": avg_s * 1e6, "back_to_back_us": b2b_s * 1e6,
+            "frac_back_to_back": per_launch / b2b_s / 1e9 / peak["hbm_gbs"], "launches": hop_n,
+            "tuned_tile_sites": tuned[0], "tuned_grid_mode": tuned[1]}
 
 
 def max_over_ranks(x: float, world: int, device) -> float:
@@ -655,25 +779,20 @@ def gpu_arm(args):
     # ---- end to end through the public API, host buffers ----
     e2e = None
     if not args.no_e2e:
-        U_stage = torch.empty_like(U_dev)
-        P_stage = torch.empty_like(P_dev)
         copy_stream = torch.cuda.Stream(dev)
-        P_copied = torch.cuda.Event()
+        P_done = torch.cuda.Event()
 
         def step_e2e():
-            # the links first (host-to-device copies share a copy engine in
-            # issue order); the propagator's copy then runs on a second stream
-            # while the source, which does not need it, is smeared
-            U_stage.copy_(U_h, non_blocking=True)
+            # host buffers through the library's own staging: the links first;
+            # the propagator's import runs on a second stream while the
+            # source, which does not need it, is smeared
+            U.import_host(U_h)
             copy_stream.wait_stream(stream)
-            with torch.cuda.stream(copy_stream):
-                P_stage.copy_(P_h, non_blocking=True)
-                P_copied.record(copy_stream)
-            U.import_(U_stage)
+            snk.import_host(P_h, stream=copy_stream)
+            P_done.record(copy_stream)
             q.point_source(src)
             q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
-            stream.wait_event(P_copied)
-            snk.import_(P_stage)
+            stream.wait_event(P_done)
             q.gauss_smear(U, snk, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
             q.meson_2pt(snk, snk, q.SIXTEEN_MESONS, out=C)
             C_h.copy_(C, non_blocking=True)
@@ -691,7 +810,13 @@ def gpu_arm(args):
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
         h2d = U_h.numel() * U_h.element_size() + P_h.numel() * P_h.element_size()
         e2e = {"value": whole_job_rate(world, b["total"], e2e_s) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": C_h.numel() * C_h.element_size(), "ms_per_step": e2e_s * 1e3}
+               "d2h_bytes_per_step": C_h.numel() * C_h.element_size(), "ms_per_step": e2e_s * 1e3,
+               "path": "qdpg_field_import_host (page-locked canonical complex64) for links and propagator, "
+                       "correlators read back every step"}
+
+    if not args.no_24x48:
+        components["hop_24x48"] = hop_24x48(q, dev, args)
+        torch.cuda.empty_cache()
 
     batch = None
     if not args.no_batch:

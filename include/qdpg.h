@@ -161,6 +161,11 @@ int qdpg_device_status(void* stream);
  *                              run out; -1 (default) = none;
  *  QDPG_DEBUG_FORCE_SIMPLE_HOP nonzero: always use the one-thread-per-site
  *                              smearing kernel without the copy pipeline;
+ *  QDPG_DEBUG_FAIL_ALLOCS      the next `value` device allocations of the library's
+ *                              temporaries fail as if the device were out of memory
+ *                              (the calls return QDPG_ERR_NOMEM); 0 = none;
+ *  QDPG_DEBUG_STAGE_BYTES      largest chunk (bytes of canonical data, at least one
+ *                              timeslice) of the host-buffer import/export; 0 = 256 MiB;
  * and launch-shape settings of the pipelined smearing kernel:
  *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..288, 0 = default;
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
@@ -178,9 +183,17 @@ enum {
   QDPG_TUNE_STAGES = 5,
   QDPG_TUNE_GRID = 7,
   QDPG_TUNE_F16_WARPS = 8,
-  QDPG_TUNE_TENSOR_COPY = 9
+  QDPG_TUNE_TENSOR_COPY = 9,
+  QDPG_DEBUG_FAIL_ALLOCS = 11,
+  QDPG_DEBUG_STAGE_BYTES = 12
 };
 int qdpg_debug_set(int what, long long value);
+
+/* Device allocations the library has made for its own temporaries in this
+ * process (smearing scratch when none is given, site values of the momentum
+ * projection, staging buffers of the host-buffer import/export).  All are
+ * stream-ordered (cudaMallocAsync) and freed on the same stream. */
+uint64_t qdpg_device_alloc_count(void);
 
 /* ---- autotuning of the smearing kernel --------------------------------------
  * The pipelined smearing kernel's tile width and grid (persistent or one CTA
@@ -234,6 +247,28 @@ int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* 
  * (reconstruct-12 gauge fields are expanded to all nine entries; F16
  * propagators are multiplied by 2^exp, which is exact). */
 int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream);
+
+/* Host-buffer forms of import and export (Sec. 5 source creation: the
+ * propagator arrives from the host, and the smeared fields and correlators
+ * go back to it).  `host_canon` is host memory in the canonical layout
+ * above (import: complex double or complex float per `canon`; export:
+ * complex double).  Same conversions as qdpg_field_import/export.
+ *  - The data moves through a device staging buffer that the library
+ *    allocates stream-ordered (cudaMallocAsync) and frees on `stream` after
+ *    the last chunk: one cudaMemcpyAsync per contiguous run of whole
+ *    timeslices (at most 256 MiB of canonical data per chunk) when
+ *    j_decay = 3, where a timeslice is contiguous in the canonical order
+ *    (four runs per chunk for a gauge field, one per direction); otherwise
+ *    the whole field in one chunk.  F16 propagators read the host data
+ *    twice (the first pass finds the largest magnitude that fixes the scale).
+ *  - Page-locked host memory (cudaHostAlloc / cudaHostRegister) keeps the
+ *    calls asynchronous; with pageable memory they are still correct but
+ *    the copies synchronise with the host.  The host buffer must stay
+ *    valid (import) or untouched (export) until `stream` has passed the call.
+ *  - QDPG_ERR_NOMEM if the staging buffer cannot be allocated; QDPG_ERR_CUDA
+ *    if a copy fails. */
+int qdpg_field_import_host(qdpg_field_t dst, const void* host_canon, int canon, void* stream);
+int qdpg_field_export_host(qdpg_field_t src, double* host_canon, void* stream);
 
 /* Point source at x0 (Sec. 5 "source creation"): zero the field, then set
  * the unit entries at x0.  PROPAGATOR: all twelve columns,

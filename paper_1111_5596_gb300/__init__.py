@@ -65,6 +65,9 @@ def load() -> ctypes.CDLL:
         "qdpg_field_release": (None, [vp]),
         "qdpg_field_import": (i, [vp, vp, i, vp]),
         "qdpg_field_export": (i, [vp, vp, vp]),
+        "qdpg_field_import_host": (i, [vp, vp, i, vp]),
+        "qdpg_field_export_host": (i, [vp, vp, vp]),
+        "qdpg_device_alloc_count": (ctypes.c_uint64, []),
         "qdpg_point_source": (i, [vp, ip, i, vp]),
         "qdpg_shift": (i, [vp, vp, i, i, vp]),
         "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
@@ -120,7 +123,13 @@ def launch_count() -> int:
 
 
 DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_STAGE, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
+DEBUG_FAIL_ALLOCS, DEBUG_STAGE_BYTES = 11, 12
 TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_GRID, TUNE_TENSOR_COPY = 4, 5, 7, 9
+
+
+def device_alloc_count() -> int:
+    """Device allocations libqdpg has made for its own temporaries in this process."""
+    return int(load().qdpg_device_alloc_count())
 
 
 def device_status(stream=None):
@@ -241,6 +250,45 @@ class Field:
         out = torch.empty(self.lattice.canonical_shape(self.kind), dtype=torch.complex128,
                           device=self.storage.device)
         _check(_lib.qdpg_field_export(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+        return out
+
+    def import_host(self, canonical, stream=None) -> "Field":
+        """Fill from a canonical-layout complex128/complex64 array in host memory
+        (numpy array or CPU tensor; page-locked memory keeps the call
+        asynchronous).  The library stages the data through its own device
+        buffer; the host array is kept alive until the stream has passed."""
+        import torch
+
+        if isinstance(canonical, np.ndarray):
+            canonical = torch.from_numpy(canonical)
+        if not isinstance(canonical, torch.Tensor) or canonical.is_cuda:
+            raise ValueError("canonical data must be a host (CPU) array")
+        if tuple(canonical.shape) != self.lattice.canonical_shape(self.kind):
+            raise ValueError(f"canonical shape {tuple(canonical.shape)} != "
+                             f"{self.lattice.canonical_shape(self.kind)}")
+        if canonical.dtype == torch.complex128:
+            ctype = CANON_F64
+        elif canonical.dtype == torch.complex64:
+            ctype = CANON_F32
+        else:
+            raise ValueError("canonical data must be complex128 or complex64")
+        canonical = canonical.contiguous()
+        _check(_lib.qdpg_field_import_host(self._h, ctypes.c_void_p(canonical.data_ptr()), ctype, _stream(stream)))
+        self._keep = canonical
+        return self
+
+    def export_host(self, out=None, stream=None):
+        """Write the field to a canonical-layout complex128 CPU tensor (page-locked
+        if ``out`` is not given).  Asynchronous: synchronise the stream before
+        reading the result."""
+        import torch
+
+        shape = self.lattice.canonical_shape(self.kind)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.complex128, pin_memory=True)
+        if out.is_cuda or out.dtype != torch.complex128 or tuple(out.shape) != shape or not out.is_contiguous():
+            raise ValueError("out must be a contiguous complex128 CPU tensor of the canonical shape")
+        _check(_lib.qdpg_field_export_host(self._h, ctypes.c_void_p(out.data_ptr()), _stream(stream)))
         return out
 
     def like(self) -> "Field":

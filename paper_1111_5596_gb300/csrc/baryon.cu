@@ -363,8 +363,8 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
   int site_scale = 1;
   if (tensor_proj) {
     void* t = nullptr;
-    if (cudaMallocAsync(&t, sizeof(float2) * (size_t)g.Nt * g.V3, s) != cudaSuccess)
-      return fail(QDPG_ERR_NOMEM, "baryon_2pt: site values for the momentum projection");
+    const int arc = dev_alloc(&t, sizeof(float2) * (size_t)g.Nt * g.V3, s, "baryon_2pt site values");
+    if (arc != QDPG_OK) return arc;
     ksites = static_cast<float2*>(t);
     site_scale = 0;
   } else if (!sites) {
@@ -404,7 +404,7 @@ int baryon_common(qdpg_field_t Su, qdpg_field_t Sd, int kind, int parity, const 
     std::vector<int> mom_flat(moms, moms + 3 * (size_t)n_mom);
     if (rc == QDPG_OK)
       rc = launch_momproj(g, ksites, 1, mom_flat.data(), n_mom, origin, out_dev, Su->rec, 2, Sd->rec, 1, s);
-    cudaFreeAsync(ksites, s);
+    dev_free(ksites, s);
   }
   return rc;
 }

@@ -50,6 +50,15 @@ __device__ __forceinline__ void load_elem(const __nv_bfloat162* p, double& re, d
   im = __bfloat162float(v.y);
 }
 
+// Whole timeslices [t0, t0 + nt) of a field whose canonical data (in the
+// buffer a kernel is given) starts at canonical site site0 and spans nsites
+// sites per direction; the whole field is {0, Nt, 0, V}.  A chunk of fewer
+// timeslices is contiguous in the canonical order when j_decay = 3.
+struct Chunk {
+  int t0, nt;
+  long long site0, nsites;
+};
+
 // Canonical complex index of device component `comp` at canonical site `site`.
 __device__ __forceinline__ long long canon_index(int kind, bool r12, int nc, long long V, long long site,
                                                  int comp) {
@@ -63,18 +72,19 @@ __device__ __forceinline__ long long canon_index(int kind, bool r12, int nc, lon
 
 template <typename Src, typename Dst>
 __global__ void __launch_bounds__(kThreads) import_kernel(Dst* __restrict__ dst, const Src* __restrict__ src,
-                                                          Geom g, int kind, bool r12, int nc) {
-  const long long total = g.V * nc;
+                                                          Geom g, int kind, bool r12, int nc, Chunk ck) {
+  const long long total = (long long)ck.nt * nc * g.V3;
+  Dst* d0 = dst + (long long)ck.t0 * nc * g.V3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int s3 = (int)(i % g.V3);
     long long r = i / g.V3;
     int comp = (int)(r % nc);
-    int t = (int)(r / nc);
-    long long site = canon_site(g, t, s3);
+    int t = ck.t0 + (int)(r / nc);
+    long long site = canon_site(g, t, s3) - ck.site0;
     int nc_canon = (kind == QDPG_GAUGE) ? 9 : nc;
-    long long ci = canon_index(kind, r12, nc_canon, g.V, site, comp);
-    store_elem(dst + i, (double)src[2 * ci], (double)src[2 * ci + 1]);
+    long long ci = canon_index(kind, r12, nc_canon, ck.nsites, site, comp);
+    store_elem(d0 + i, (double)src[2 * ci], (double)src[2 * ci + 1]);
   }
 }
 
@@ -82,17 +92,17 @@ __global__ void __launch_bounds__(kThreads) import_kernel(Dst* __restrict__ dst,
 template <typename Dev>
 __global__ void __launch_bounds__(kThreads) export_kernel(double* __restrict__ out, const Dev* __restrict__ dev,
                                                           Geom g, int kind, bool r12, int nc,
-                                                          const ScaleRecord* rec) {
+                                                          const ScaleRecord* rec, Chunk ck) {
   const int e2 = rec ? rec->exp : 0;  // value = stored * 2^exp
   const int nc_canon = (kind == QDPG_GAUGE) ? 9 : nc;
   const long long nmu = (kind == QDPG_GAUGE) ? 4 : 1;
-  const long long total = nmu * g.V * nc_canon;
+  const long long total = nmu * ck.nsites * nc_canon;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int e = (int)(i % nc_canon);
     long long r = i / nc_canon;
-    long long site = r % g.V;
-    int mu = (int)(r / g.V);
+    long long site = ck.site0 + r % ck.nsites;
+    int mu = (int)(r / ck.nsites);
     // canonical site -> (t, s3)
     int x[4];
     long long rr = site;
@@ -210,16 +220,17 @@ __global__ void __launch_bounds__(kThreads) f16_max_kernel(const Src* __restrict
 
 template <typename Src>
 __global__ void __launch_bounds__(kThreads) f16_import_kernel(__half2* __restrict__ dst, const Src* __restrict__ src,
-                                                              Geom g, ScaleRecord* rec) {
+                                                              Geom g, ScaleRecord* rec, Chunk ck) {
   const float m = __uint_as_float(rec->tmpmax);
   const int e = f16_exp_for(m);
-  const long long total = g.V * 144;
+  const long long total = (long long)ck.nt * 144 * g.V3;
+  const long long w0 = (long long)ck.t0 * 144 * g.V3;  // a timeslice's words are contiguous
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int t, s3, comp;
-    f16_word_decode(i, g.V3, t, s3, comp);
-    const long long ci = canon_site(g, t, s3) * 144 + comp;
-    store_elem(dst + i, ldexp((double)src[2 * ci], -e), ldexp((double)src[2 * ci + 1], -e));
+    f16_word_decode(w0 + i, g.V3, t, s3, comp);
+    const long long ci = (canon_site(g, t, s3) - ck.site0) * 144 + comp;
+    store_elem(dst + w0 + i, ldexp((double)src[2 * ci], -e), ldexp((double)src[2 * ci + 1], -e));
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     rec->exp = e;
@@ -228,16 +239,17 @@ __global__ void __launch_bounds__(kThreads) f16_import_kernel(__half2* __restric
 }
 
 __global__ void __launch_bounds__(kThreads) f16_export_kernel(double* __restrict__ out, const __half2* __restrict__ dev,
-                                                              Geom g, const ScaleRecord* rec) {
+                                                              Geom g, const ScaleRecord* rec, Chunk ck) {
   const int e = rec->exp;
-  const long long total = g.V * 144;
+  const long long total = (long long)ck.nt * 144 * g.V3;
+  const long long w0 = (long long)ck.t0 * 144 * g.V3;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
        i += (long long)gridDim.x * blockDim.x) {
     int t, s3, comp;
-    f16_word_decode(i, g.V3, t, s3, comp);
-    const long long ci = canon_site(g, t, s3) * 144 + comp;
+    f16_word_decode(w0 + i, g.V3, t, s3, comp);
+    const long long ci = (canon_site(g, t, s3) - ck.site0) * 144 + comp;
     double re, im;
-    load_elem(dev + i, re, im);
+    load_elem(dev + w0 + i, re, im);
     out[2 * ci] = ldexp(re, e);
     out[2 * ci + 1] = ldexp(im, e);
   }
@@ -294,6 +306,132 @@ __global__ void __launch_bounds__(kThreads) f16_shift_kernel(uint32_t* __restric
 
 }  // namespace qdpg
 
+namespace qdpg {
+namespace {
+
+// Conversion of one chunk of canonical data (device memory) into dst's
+// layout.  F16 propagators: pass 0 folds the chunk's largest magnitude into
+// the scale record's scratch, pass 1 converts with the scale that the
+// whole field's maximum fixes.
+int import_chunk(qdpg_field_t dst, const void* canon_dev, int canon, const Chunk& ck, int f16_pass, cudaStream_t s) {
+  const long long total = (long long)ck.nt * dst->ncomp * dst->g.V3;
+  const bool r12 = is_r12(dst->prec);
+  const int grid = grid_for(total);
+  const bool f64 = canon == QDPG_CANON_F64;
+  ProfScope prof("field_import", s);
+  if (is_f16_prop(dst)) {
+    auto* d = static_cast<__half2*>(dst->data);
+    const long long nreal = 2 * ck.nsites * 144;
+    if (f16_pass == 0) {
+      if (f64)
+        f16_max_kernel<<<grid_for(nreal), kThreads, 0, s>>>(static_cast<const double*>(canon_dev), nreal,
+                                                            &dst->rec->tmpmax);
+      else
+        f16_max_kernel<<<grid_for(nreal), kThreads, 0, s>>>(static_cast<const float*>(canon_dev), nreal,
+                                                            &dst->rec->tmpmax);
+    } else if (f64) {
+      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->rec, ck);
+    } else {
+      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->rec, ck);
+    }
+    return check_launch("field_import");
+  }
+#define QDPG_IMPORT(DT)                                                                                          \
+  do {                                                                                                           \
+    auto* d = static_cast<DT*>(dst->data);                                                                       \
+    if (f64)                                                                                                     \
+      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind, \
+                                                      r12, dst->ncomp, ck);                                      \
+    else                                                                                                         \
+      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,   \
+                                                     r12, dst->ncomp, ck);                                       \
+  } while (0)
+  if (is_f16(dst->prec))
+    QDPG_IMPORT(__half2);
+  else if (is_bf16(dst->prec))
+    QDPG_IMPORT(__nv_bfloat162);
+  else
+    QDPG_IMPORT(float2);
+#undef QDPG_IMPORT
+  return check_launch("field_import");
+}
+
+// Before the first chunk: clear the F16 maximum.  After the last: imported
+// F32/BF16 values are unscaled, exp = 0 (F16 import kernels set their exp).
+int import_begin(qdpg_field_t dst, cudaStream_t s) {
+  if (!is_f16_prop(dst)) return QDPG_OK;
+  const cudaError_t e = cudaMemsetAsync(&dst->rec->tmpmax, 0, sizeof(unsigned), s);
+  return e == cudaSuccess ? QDPG_OK : fail(QDPG_ERR_CUDA, "field_import: memset: %s", cudaGetErrorString(e));
+}
+int import_end(qdpg_field_t dst, cudaStream_t s) {
+  if (!dst->rec || is_f16_prop(dst)) return QDPG_OK;
+  const cudaError_t e = cudaMemsetAsync(dst->rec, 0, 2 * sizeof(int), s);
+  return e == cudaSuccess ? QDPG_OK : fail(QDPG_ERR_CUDA, "field_import: scale reset: %s", cudaGetErrorString(e));
+}
+
+int export_chunk(qdpg_field_t src, double* canon_dev, const Chunk& ck, cudaStream_t s) {
+  const long long total = (src->kind == QDPG_GAUGE ? 4 * 9 : src->ncomp) * ck.nsites;
+  const int grid = grid_for(total);
+  const bool r12 = is_r12(src->prec);
+  ProfScope prof("field_export", s);
+  if (is_f16_prop(src))
+    f16_export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->rec,
+                                                ck);
+  else if (is_f16(src->prec))
+    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->kind,
+                                            r12, src->ncomp, src->rec, ck);
+  else if (is_bf16(src->prec))
+    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __nv_bfloat162*>(src->data), src->g,
+                                            src->kind, r12, src->ncomp, src->rec, ck);
+  else
+    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const float2*>(src->data), src->g, src->kind,
+                                            r12, src->ncomp, src->rec, ck);
+  return check_launch("field_export");
+}
+
+Chunk whole_field(const Geom& g) { return Chunk{0, g.Nt, 0, g.V}; }
+
+// Complex numbers per site in the canonical layout (all four links of a gauge field).
+long long canon_per_site(const qdpg_field* f) { return f->kind == QDPG_GAUGE ? 36 : f->ncomp; }
+
+// Host transfers: chunks of whole timeslices of at most 256 MiB of
+// canonical data (or the QDPG_DEBUG_STAGE_BYTES setting) when j_decay = 3,
+// else the whole field.
+int chunk_timeslices(const qdpg_field* f, size_t csize) {
+  if (f->g.jd != 3) return f->g.Nt;
+  const size_t per_t = (size_t)f->g.V3 * canon_per_site(f) * csize;
+  const long long limit = debug_stage_bytes() > 0 ? debug_stage_bytes() : (256LL << 20);
+  long long n = (long long)(limit / (long long)per_t);
+  if (n < 1) n = 1;
+  if (n > f->g.Nt) n = f->g.Nt;
+  return (int)n;
+}
+Chunk chunk_at(const qdpg_field* f, int t0, int nt) {
+  if (f->g.jd != 3) return whole_field(f->g);
+  return Chunk{t0, nt, (long long)t0 * f->g.V3, (long long)nt * f->g.V3};
+}
+
+// Copy a chunk between the host canonical buffer and the staging buffer
+// (one run per link direction for a gauge field).
+int copy_chunk(const qdpg_field* f, void* stage, const void* host, const Chunk& ck, size_t csize, bool to_device,
+               cudaStream_t s) {
+  const int nmu = f->kind == QDPG_GAUGE ? 4 : 1;
+  const long long per = f->kind == QDPG_GAUGE ? 9 : f->ncomp;  // complex numbers per site and direction
+  const size_t run = (size_t)ck.nsites * per * csize;
+  for (int mu = 0; mu < nmu; ++mu) {
+    const size_t hoff = ((size_t)mu * f->g.V + ck.site0) * per * csize;
+    char* dptr = static_cast<char*>(stage) + mu * run;
+    const char* hptr = static_cast<const char*>(host) + hoff;
+    const cudaError_t e = to_device ? cudaMemcpyAsync(dptr, hptr, run, cudaMemcpyHostToDevice, s)
+                                    : cudaMemcpyAsync(const_cast<char*>(hptr), dptr, run, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "field host copy: %s", cudaGetErrorString(e));
+  }
+  return QDPG_OK;
+}
+
+}  // namespace
+}  // namespace qdpg
+
 using namespace qdpg;
 
 extern "C" {
@@ -303,80 +441,58 @@ int qdpg_field_import(qdpg_field_t dst, const void* canon_dev, int canon, void* 
   if (canon != QDPG_CANON_F64 && canon != QDPG_CANON_F32)
     return fail(QDPG_ERR_DTYPE, "field_import: canonical type %d unknown", canon);
   cudaStream_t s = as_stream(stream);
-  const long long total = dst->g.V * dst->ncomp;
-  const bool r12 = is_r12(dst->prec);
-  const int grid = grid_for(total);
-  if (is_f16_prop(dst)) {
-    // largest |re|, |im| first: it fixes the power-of-two scale of the data
-    cudaError_t e = cudaMemsetAsync(&dst->rec->tmpmax, 0, sizeof(unsigned), s);
-    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "field_import: memset: %s", cudaGetErrorString(e));
-    ProfScope prof("field_import", s);
-    auto* d = static_cast<__half2*>(dst->data);
-    if (canon == QDPG_CANON_F64) {
-      f16_max_kernel<<<grid_for(2 * total), kThreads, 0, s>>>(static_cast<const double*>(canon_dev), 2 * total,
-                                                              &dst->rec->tmpmax);
-      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->rec);
-    } else {
-      f16_max_kernel<<<grid_for(2 * total), kThreads, 0, s>>>(static_cast<const float*>(canon_dev), 2 * total,
-                                                              &dst->rec->tmpmax);
-      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->rec);
-    }
-    count_launches(1);
-    return check_launch("field_import");
-  }
-  ProfScope prof("field_import", s);
-  if (is_f16(dst->prec)) {
-    auto* d = static_cast<__half2*>(dst->data);
-    if (canon == QDPG_CANON_F64)
-      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
-                                                      r12, dst->ncomp);
-    else
-      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
-                                                     r12, dst->ncomp);
-  } else if (is_bf16(dst->prec)) {
-    auto* d = static_cast<__nv_bfloat162*>(dst->data);
-    if (canon == QDPG_CANON_F64)
-      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
-                                                      r12, dst->ncomp);
-    else
-      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
-                                                     r12, dst->ncomp);
-  } else {
-    auto* d = static_cast<float2*>(dst->data);
-    if (canon == QDPG_CANON_F64)
-      import_kernel<double><<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->kind,
-                                                      r12, dst->ncomp);
-    else
-      import_kernel<float><<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->kind,
-                                                     r12, dst->ncomp);
-  }
-  const int rc = check_launch("field_import");
-  if (rc == QDPG_OK && dst->rec) {  // imported values are unscaled: exp = 0
-    cudaError_t e = cudaMemsetAsync(dst->rec, 0, 2 * sizeof(int), s);
-    if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "field_import: scale reset: %s", cudaGetErrorString(e));
-  }
+  const Chunk all = whole_field(dst->g);
+  int rc = import_begin(dst, s);
+  if (rc == QDPG_OK && is_f16_prop(dst)) rc = import_chunk(dst, canon_dev, canon, all, 0, s);
+  if (rc == QDPG_OK) rc = import_chunk(dst, canon_dev, canon, all, 1, s);
+  if (rc == QDPG_OK) rc = import_end(dst, s);
   return rc;
 }
 
 int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream) {
   if (!src || !canon_dev) return fail(QDPG_ERR_ARG, "field_export: null argument");
+  return export_chunk(src, canon_dev, whole_field(src->g), as_stream(stream));
+}
+
+int qdpg_field_import_host(qdpg_field_t dst, const void* host_canon, int canon, void* stream) {
+  if (!dst || !host_canon) return fail(QDPG_ERR_ARG, "field_import_host: null argument");
+  if (canon != QDPG_CANON_F64 && canon != QDPG_CANON_F32)
+    return fail(QDPG_ERR_DTYPE, "field_import_host: canonical type %d unknown", canon);
   cudaStream_t s = as_stream(stream);
-  const long long total = (src->kind == QDPG_GAUGE ? 4 * 9 : src->ncomp) * src->g.V;
-  const int grid = grid_for(total);
-  const bool r12 = is_r12(src->prec);
-  ProfScope prof("field_export", s);
-  if (is_f16_prop(src))
-    f16_export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->rec);
-  else if (is_f16(src->prec))
-    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __half2*>(src->data), src->g, src->kind,
-                                            r12, src->ncomp, src->rec);
-  else if (is_bf16(src->prec))
-    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const __nv_bfloat162*>(src->data), src->g,
-                                            src->kind, r12, src->ncomp, src->rec);
-  else
-    export_kernel<<<grid, kThreads, 0, s>>>(canon_dev, static_cast<const float2*>(src->data), src->g, src->kind,
-                                            r12, src->ncomp, src->rec);
-  return check_launch("field_export");
+  const size_t csize = canon == QDPG_CANON_F64 ? 16 : 8;
+  const int ntc = chunk_timeslices(dst, csize);
+  void* stage = nullptr;
+  int rc = dev_alloc(&stage, (size_t)ntc * dst->g.V3 * canon_per_site(dst) * csize, s, "field_import_host staging");
+  if (rc != QDPG_OK) return rc;
+  rc = import_begin(dst, s);
+  for (int pass = is_f16_prop(dst) ? 0 : 1; pass <= 1 && rc == QDPG_OK; ++pass)
+    for (int t0 = 0; t0 < dst->g.Nt && rc == QDPG_OK; t0 += ntc) {
+      const Chunk ck = chunk_at(dst, t0, ntc < dst->g.Nt - t0 ? ntc : dst->g.Nt - t0);
+      rc = copy_chunk(dst, stage, host_canon, ck, csize, true, s);
+      if (rc == QDPG_OK) rc = import_chunk(dst, stage, canon, ck, pass, s);
+      if (dst->g.jd != 3) break;  // one chunk: the whole field
+    }
+  if (rc == QDPG_OK) rc = import_end(dst, s);
+  dev_free(stage, s);
+  return rc;
+}
+
+int qdpg_field_export_host(qdpg_field_t src, double* host_canon, void* stream) {
+  if (!src || !host_canon) return fail(QDPG_ERR_ARG, "field_export_host: null argument");
+  cudaStream_t s = as_stream(stream);
+  const size_t csize = 16;
+  const int ntc = chunk_timeslices(src, csize);
+  void* stage = nullptr;
+  int rc = dev_alloc(&stage, (size_t)ntc * src->g.V3 * canon_per_site(src) * csize, s, "field_export_host staging");
+  if (rc != QDPG_OK) return rc;
+  for (int t0 = 0; t0 < src->g.Nt && rc == QDPG_OK; t0 += ntc) {
+    const Chunk ck = chunk_at(src, t0, ntc < src->g.Nt - t0 ? ntc : src->g.Nt - t0);
+    rc = export_chunk(src, static_cast<double*>(stage), ck, s);
+    if (rc == QDPG_OK) rc = copy_chunk(src, stage, host_canon, ck, csize, false, s);
+    if (src->g.jd != 3) break;
+  }
+  dev_free(stage, s);
+  return rc;
 }
 
 int qdpg_point_source(qdpg_field_t f, const int x0[4], int spin_color, void* stream) {

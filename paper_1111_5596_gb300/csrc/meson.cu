@@ -393,9 +393,11 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
       const size_t out_bytes = sizeof(double) * 2 * (size_t)L.nch * n_mom * g.Nt;
       void* tsites = nullptr;
       void* tout = nullptr;
-      if (cudaMallocAsync(&tsites, site_bytes, s) != cudaSuccess || cudaMallocAsync(&tout, out_bytes, s) != cudaSuccess) {
-        if (tsites) cudaFreeAsync(tsites, s);
-        return fail(QDPG_ERR_NOMEM, "meson_2pt: %zu bytes of site values for the momentum projection", site_bytes);
+      int arc = dev_alloc(&tsites, site_bytes, s, "meson_2pt site values");
+      if (arc == QDPG_OK) arc = dev_alloc(&tout, out_bytes, s, "meson_2pt projected sums");
+      if (arc != QDPG_OK) {
+        dev_free(tsites, s);
+        return arc;
       }
       rc = launch_pass(L, M, S1, S2, nullptr, static_cast<float2*>(tsites), s, 0);
       if (rc == QDPG_OK)
@@ -407,8 +409,8 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
                                         static_cast<char*>(tout) + blk * j, blk, cudaMemcpyDeviceToDevice, s);
         if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "meson_2pt: copy: %s", cudaGetErrorString(e));
       }
-      cudaFreeAsync(tsites, s);
-      cudaFreeAsync(tout, s);
+      dev_free(tsites, s);
+      dev_free(tout, s);
     }
     P = MesonPass{};
     return rc;

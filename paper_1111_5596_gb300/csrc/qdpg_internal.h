@@ -103,6 +103,12 @@ int debug_tile_stages();     // pipeline depth, 0 = as many as fit the shared-me
 int debug_tile_grid();       // 0: persistent CTAs, 1: one CTA per work item
 int debug_tensor_copy_off();  // 1: no tensor-map copies in the pipelined FP32/BF16 hop
 int debug_f16_warps();       // consumer warps of the float16 smearing kernel, 0 = default
+// Stream-ordered device allocation of the library's temporaries (every
+// allocation goes through here): QDPG_ERR_NOMEM with a message naming
+// `what` on failure, including failures forced by QDPG_DEBUG_FAIL_ALLOCS.
+int dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
+long long debug_stage_bytes();  // chunk bound of the host-buffer import/export, 0 = default
+void dev_free(void* p, cudaStream_t s);
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage
 constexpr unsigned int kStatusDrain = 4u;      // producer gave up draining its own copies

@@ -160,9 +160,8 @@ int gauss_smear_f16(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, 
   void* tmp = scratch ? scratch->data : nullptr;
   bool owned = false;
   if (!tmp) {
-    cudaError_t e = cudaMallocAsync(&tmp, bytes, s);
-    if (e != cudaSuccess) return fail(QDPG_ERR_NOMEM, "gauss_smear: scratch allocation of %zu bytes: %s", bytes,
-                                      cudaGetErrorString(e));
+    const int rc = dev_alloc(&tmp, bytes, s, "gauss_smear scratch");
+    if (rc != QDPG_OK) return rc;
     owned = true;
   }
   ScaleRecord* rec = psi->rec;
@@ -177,7 +176,7 @@ int gauss_smear_f16(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, 
     cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "gauss_smear: copy-back: %s", cudaGetErrorString(e));
   }
-  if (owned) cudaFreeAsync(tmp, s);
+  if (owned) dev_free(tmp, s);
   return rc;
 }
 
@@ -215,44 +214,28 @@ int launch_hop_any(const void* in, void* out, const void* U, int lprec, int psi_
   return launch_hop<float2>(in, out, U, lprec, g, hd, kappa, cols, s);
 }
 
-}  // namespace qdpg
-
-using namespace qdpg;
-
-extern "C" {
-
-int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay, qdpg_field_t scratch,
-                     void* stream) {
-  if (!U || !psi) return fail(QDPG_ERR_ARG, "gauss_smear: null field");
-  if (U->kind != QDPG_GAUGE) return fail(QDPG_ERR_SHAPE, "gauss_smear: U must be a gauge field");
+// Argument checks shared by the smearing entry points.
+int check_smear_args(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay, const char* who) {
+  if (!U || !psi) return fail(QDPG_ERR_ARG, "%s: null field", who);
+  if (U->kind != QDPG_GAUGE) return fail(QDPG_ERR_SHAPE, "%s: U must be a gauge field", who);
   if (psi->kind != QDPG_PROPAGATOR && psi->kind != QDPG_FERMION)
-    return fail(QDPG_ERR_SHAPE, "gauss_smear: psi must be a propagator or fermion");
+    return fail(QDPG_ERR_SHAPE, "%s: psi must be a propagator or fermion", who);
   if (psi->prec != QDPG_F32 && psi->prec != QDPG_BF16 && psi->prec != QDPG_F16)
-    return fail(QDPG_ERR_DTYPE, "gauss_smear: psi storage must be F32, BF16 or F16");
-  if (!same_lattice(U->g, psi->g)) return fail(QDPG_ERR_SHAPE, "gauss_smear: U and psi on different lattices");
+    return fail(QDPG_ERR_DTYPE, "%s: psi storage must be F32, BF16 or F16", who);
+  if (!same_lattice(U->g, psi->g)) return fail(QDPG_ERR_SHAPE, "%s: U and psi on different lattices", who);
   if ((psi->prec == QDPG_F16) != is_f16(U->prec))
-    return fail(QDPG_ERR_DTYPE, "gauss_smear: F16 propagators go with F16/F16_R12 links and only with them");
-  if (j_decay < 0 || j_decay > 3) return fail(QDPG_ERR_ARG, "gauss_smear: j_decay %d outside 0..3", j_decay);
-  if (n_iter < 0) return fail(QDPG_ERR_ARG, "gauss_smear: negative iteration count");
-  if (!(kappa == kappa) || kappa > 1e30 || kappa < -1e30) return fail(QDPG_ERR_ARG, "gauss_smear: kappa not finite");
-  if (scratch) {
-    if (scratch->kind != psi->kind || scratch->prec != psi->prec || !same_lattice(scratch->g, psi->g))
-      return fail(QDPG_ERR_SHAPE, "gauss_smear: scratch differs from psi in kind/precision/lattice");
-    if (scratch->data == psi->data) return fail(QDPG_ERR_ARG, "gauss_smear: scratch aliases psi");
-  }
-  if (n_iter == 0) return ok();
-  if (psi->prec == QDPG_F16) return gauss_smear_f16(U, psi, kappa, n_iter, j_decay, scratch, as_stream(stream));
+    return fail(QDPG_ERR_DTYPE, "%s: F16 propagators go with F16/F16_R12 links and only with them", who);
+  if (j_decay < 0 || j_decay > 3) return fail(QDPG_ERR_ARG, "%s: j_decay %d outside 0..3", who, j_decay);
+  if (n_iter < 0) return fail(QDPG_ERR_ARG, "%s: negative iteration count", who);
+  if (!(kappa == kappa) || kappa > 1e30 || kappa < -1e30) return fail(QDPG_ERR_ARG, "%s: kappa not finite", who);
+  return QDPG_OK;
+}
 
-  cudaStream_t s = as_stream(stream);
-  const size_t bytes = (size_t)psi->g.V * psi->ncomp * psi->esize;
-  void* tmp = scratch ? scratch->data : nullptr;
-  bool owned = false;
-  if (!tmp) {
-    cudaError_t e = cudaMallocAsync(&tmp, bytes, s);
-    if (e != cudaSuccess) return fail(QDPG_ERR_NOMEM, "gauss_smear: scratch allocation of %zu bytes: %s", bytes,
-                                      cudaGetErrorString(e));
-    owned = true;
-  }
+// n_iter FP32/BF16 hops of psi with tmp (a buffer of psi's data size) as
+// the other half of the ping-pong pair, the power-of-two rescaling where the
+// growth bound needs it, and the copy back into psi after an odd count.
+int smear_loop(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay, void* tmp, cudaStream_t s,
+               const char* who) {
   HopDirs hd;
   int k = 0;
   for (int mu = 0; mu < 4; ++mu)
@@ -272,10 +255,41 @@ int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter,
       rc = launch_rescale(out, psi->prec, psi->g.V * psi->ncomp, plan.shift, psi->rec, s);
   }
   if (rc == QDPG_OK && (n_iter & 1)) {
-    cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "gauss_smear: copy-back: %s", cudaGetErrorString(e));
+    const cudaError_t e =
+        cudaMemcpyAsync(psi->data, tmp, (size_t)psi->g.V * psi->ncomp * psi->esize, cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "%s: copy-back: %s", who, cudaGetErrorString(e));
   }
-  if (owned) cudaFreeAsync(tmp, s);
+  return rc;
+}
+
+}  // namespace qdpg
+
+using namespace qdpg;
+
+extern "C" {
+
+int qdpg_gauss_smear(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay, qdpg_field_t scratch,
+                     void* stream) {
+  int rc = check_smear_args(U, psi, kappa, n_iter, j_decay, "gauss_smear");
+  if (rc != QDPG_OK) return rc;
+  if (scratch) {
+    if (scratch->kind != psi->kind || scratch->prec != psi->prec || !same_lattice(scratch->g, psi->g))
+      return fail(QDPG_ERR_SHAPE, "gauss_smear: scratch differs from psi in kind/precision/lattice");
+    if (scratch->data == psi->data) return fail(QDPG_ERR_ARG, "gauss_smear: scratch aliases psi");
+  }
+  if (n_iter == 0) return ok();
+  if (psi->prec == QDPG_F16) return gauss_smear_f16(U, psi, kappa, n_iter, j_decay, scratch, as_stream(stream));
+
+  cudaStream_t s = as_stream(stream);
+  void* tmp = scratch ? scratch->data : nullptr;
+  bool owned = false;
+  if (!tmp) {
+    rc = dev_alloc(&tmp, (size_t)psi->g.V * psi->ncomp * psi->esize, s, "gauss_smear scratch");
+    if (rc != QDPG_OK) return rc;
+    owned = true;
+  }
+  rc = smear_loop(U, psi, kappa, n_iter, j_decay, tmp, s, "gauss_smear");
+  if (owned) dev_free(tmp, s);
   return rc;
 }
 
@@ -327,17 +341,10 @@ int static_scratch_address(void** out) {
 
 extern "C" int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double kappa, int n_iter, int j_decay,
                                         void* stream) {
-  if (!U || !psi) return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: null field");
-  if (U->kind != QDPG_GAUGE) return fail(QDPG_ERR_SHAPE, "gauss_smear_noalloc: U must be a gauge field");
-  if (psi->kind != QDPG_PROPAGATOR && psi->kind != QDPG_FERMION)
-    return fail(QDPG_ERR_SHAPE, "gauss_smear_noalloc: psi must be a propagator or fermion");
+  int rc = check_smear_args(U, psi, kappa, n_iter, j_decay, "gauss_smear_noalloc");
+  if (rc != QDPG_OK) return rc;
   if (psi->prec != QDPG_F32 && psi->prec != QDPG_BF16)
     return fail(QDPG_ERR_DTYPE, "gauss_smear_noalloc: psi storage must be F32 or BF16");
-  if (!same_lattice(U->g, psi->g)) return fail(QDPG_ERR_SHAPE, "gauss_smear_noalloc: U and psi on different lattices");
-  if (j_decay < 0 || j_decay > 3) return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: j_decay %d outside 0..3", j_decay);
-  if (n_iter < 0) return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: negative iteration count");
-  if (!(kappa == kappa) || kappa > 1e30 || kappa < -1e30)
-    return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: kappa not finite");
   const size_t bytes = (size_t)psi->g.V * psi->ncomp * psi->esize;
   if (bytes > kStaticScratchBytes)
     return fail(QDPG_ERR_ARG, "gauss_smear_noalloc: field of %zu bytes exceeds the %zu-byte static scratch", bytes,
@@ -345,31 +352,9 @@ extern "C" int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double
   if (n_iter == 0) return ok();
 
   void* tmp = nullptr;
-  int rc = static_scratch_address(&tmp);
+  rc = static_scratch_address(&tmp);
   if (rc) return rc;
   // The scratch is written in full by the first iteration before it is read,
   // so stale contents of an earlier call never leak into this one.
-  cudaStream_t s = as_stream(stream);
-  HopDirs hd;
-  int k = 0;
-  for (int mu = 0; mu < 4; ++mu)
-    if (mu != j_decay) hd.mu[k++] = mu;
-  const int cols = psi->kind == QDPG_PROPAGATOR ? 12 : 1;
-  void* bufs[2] = {psi->data, tmp};
-  const RescalePlan plan = rescale_plan((float)kappa, n_iter);  // the kernel's kappa
-  for (int it = 0; it < n_iter && rc == QDPG_OK; ++it) {
-    const void* in = bufs[it & 1];
-    void* out = bufs[(it + 1) & 1];
-    if (psi->prec == QDPG_BF16)
-      rc = launch_hop<__nv_bfloat162>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
-    else
-      rc = launch_hop<float2>(in, out, U->data, U->prec, psi->g, hd, (float)kappa, cols, s);
-    if (rc == QDPG_OK && plan.every && (it + 1) % plan.every == 0)
-      rc = launch_rescale(out, psi->prec, psi->g.V * psi->ncomp, plan.shift, psi->rec, s);
-  }
-  if (rc == QDPG_OK && (n_iter & 1)) {
-    cudaError_t e = cudaMemcpyAsync(psi->data, tmp, bytes, cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "gauss_smear_noalloc: copy-back: %s", cudaGetErrorString(e));
-  }
-  return rc;
+  return smear_loop(U, psi, kappa, n_iter, j_decay, tmp, as_stream(stream), "gauss_smear_noalloc");
 }

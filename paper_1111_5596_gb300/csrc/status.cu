@@ -1,5 +1,6 @@
 // Device-side status word: kernels whose bounded waits give up record it here
 // (never trap), and the host reads it back through qdpg_device_status.
+#include <atomic>
 #include <mutex>
 
 #include "qdpg_internal.h"
@@ -21,6 +22,9 @@ int g_tile_stages = 0;
 int g_tile_grid = 0;
 int g_f16_warps = 0;  // 0: the library's default (16)
 int g_tensor_copy_off = 0;  // 1: the pipelined hop stages with bulk copies only
+int g_fail_allocs = 0;      // the next this many device allocations fail (test hook)
+long long g_stage_bytes = 0;  // host import/export chunk bound, 0 = default
+std::atomic<uint64_t> g_allocs{0};
 
 }  // namespace
 
@@ -44,12 +48,38 @@ int debug_tile_stages() { return g_tile_stages; }
 int debug_tile_grid() { return g_tile_grid; }
 int debug_f16_warps() { return g_f16_warps; }
 int debug_tensor_copy_off() { return g_tensor_copy_off; }
+long long debug_stage_bytes() { return g_stage_bytes; }
+
+int dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
+  *p = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_fail_allocs > 0) {
+      --g_fail_allocs;
+      return fail(QDPG_ERR_NOMEM, "%s: allocation of %zu bytes refused (test hook)", what, bytes);
+    }
+  }
+  const cudaError_t e = cudaMallocAsync(p, bytes, s);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();  // the failed allocation leaves no sticky error
+    return fail(QDPG_ERR_NOMEM, "%s: allocation of %zu bytes: %s", what, bytes, cudaGetErrorString(e));
+  }
+  g_allocs.fetch_add(1, std::memory_order_relaxed);
+  return QDPG_OK;
+}
+
+void dev_free(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
 
 }  // namespace qdpg
 
 using namespace qdpg;
 
 extern "C" {
+
+uint64_t qdpg_device_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
 
 int qdpg_device_status(void* stream) {
   unsigned int* w = device_status_word();
@@ -98,6 +128,14 @@ int qdpg_debug_set(int what, long long value) {
     case QDPG_TUNE_TENSOR_COPY:
       if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: tensor-copy setting outside 0..1");
       g_tensor_copy_off = (int)value;
+      return ok();
+    case QDPG_DEBUG_STAGE_BYTES:
+      if (value < 0 || value > (1LL << 40)) return fail(QDPG_ERR_ARG, "debug_set: staging bytes outside 0..2^40");
+      g_stage_bytes = value;
+      return ok();
+    case QDPG_DEBUG_FAIL_ALLOCS:
+      if (value < 0 || value > 1000000) return fail(QDPG_ERR_ARG, "debug_set: failing allocations outside 0..1e6");
+      g_fail_allocs = (int)value;
       return ok();
     case QDPG_TUNE_GRID:
       if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: grid mode outside 0..1");

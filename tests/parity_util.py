@@ -18,6 +18,22 @@ def field_err(a, ref) -> float:
     return float(np.linalg.norm((a - ref).ravel()) / np.linalg.norm(ref.ravel()))
 
 
+def field_err_t(a, ref, t_axis: int = 0) -> float:
+    """Largest per-timeslice relative error: max over t of ||a_t - r_t|| / ||r_t||.
+
+    A smeared field's magnitude varies by orders of magnitude between
+    timeslices (the source envelope), so an error confined to the small
+    timeslices hardly moves the global norm; this one sees it."""
+    a = np.moveaxis(np.asarray(a), t_axis, 0)
+    ref = np.moveaxis(np.asarray(ref), t_axis, 0)
+    d = np.linalg.norm((a - ref).reshape(a.shape[0], -1), axis=1)
+    n = np.linalg.norm(ref.reshape(ref.shape[0], -1), axis=1)
+    # a timeslice the reference leaves at zero (a point source's other timeslices)
+    # is measured against the largest timeslice norm
+    n = np.where(n > 1e-12 * n.max(), n, n.max())
+    return float((d / n).max())
+
+
 def corr_err(C, C_ref) -> float:
     C = np.asarray(C)
     C_ref = np.asarray(C_ref)

@@ -240,3 +240,14 @@ def test_tuning_settings_are_validated_on_host(q):
     finally:
         for what in (TILE, STAGES, F16_WARPS, TENSOR_COPY):
             assert L.qdpg_debug_set(what, 0) == OK
+
+
+def test_host_io_and_alloc_hooks_validate_on_host(q):
+    lib = q._lib
+    assert lib.qdpg_field_import_host(None, None, 0, None) == ERR_ARG
+    assert lib.qdpg_field_export_host(None, None, None) == ERR_ARG
+    assert lib.qdpg_debug_set(q.DEBUG_FAIL_ALLOCS, -1) == ERR_ARG
+    assert lib.qdpg_debug_set(q.DEBUG_STAGE_BYTES, -5) == ERR_ARG
+    assert lib.qdpg_debug_set(q.DEBUG_FAIL_ALLOCS, 0) == OK
+    assert lib.qdpg_debug_set(q.DEBUG_STAGE_BYTES, 0) == OK
+    assert isinstance(q.device_alloc_count(), int)

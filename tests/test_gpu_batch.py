@@ -13,7 +13,7 @@ import torch
 
 from oracle import hadron, smear
 from synth import fields
-from tests.parity_util import TOL_BF16, TOL_F32, corr_err, field_err, to_bf16_complex
+from tests.parity_util import TOL_BF16, TOL_F32, corr_err, field_err, field_err_t, to_bf16_complex
 
 pytestmark = pytest.mark.gpu
 
@@ -85,7 +85,7 @@ def test_batch_matches_oracle_and_single_job_path(qdpg_gpu):
         if r["n"] == 0:
             assert np.array_equal(out, r["psi"])
         else:
-            assert field_err(out, ref) <= tol
+            assert field_err(out, ref) <= tol and field_err_t(out, ref) <= tol
         # the one-job entry point gives the same bits
         g = r["f"].like().import_(torch.from_numpy(r["psi"].astype(np.complex64)).to(DEV))
         q.gauss_smear(r["Uf"], g, r["kappa"], r["n"], 3, scratch=g.like())

@@ -6,24 +6,26 @@ FP32 storage and in float16 storage (per-field power-of-two scale, float16
 reconstruct-12 links, tensor-core hop).
 
 For each lattice size the job with the most iterations is checked against
-the FP64 checker on timeslice 0 (smearing and contractions never couple
-timeslices, so one timeslice is exact), and against the one-job entry
-point bit for bit (FP32).  Correlator errors on that one timeslice are per
-channel |C - C_ref| / |C_ref| for FP32, and relative to A = sum_x |c(x)| for
-float16: a single timeslice sum of a synthetic propagator's non-pion
-channel cancels strongly, and stored values with 11 significant bits bound
-the error of such a sum relative to A (8^3 job, N = 44: 4.4e-2 of |C_ref|,
-~1e-3 of A).  Over all timeslices, every float16 job's correlators stay
-within the reduced-precision bound of FP32's, per channel.
+the FP64 checker on every timeslice (the checker runs timeslice by
+timeslice on a spawned process pool over the host cores: smearing and
+contractions never couple timeslices), and against the one-job entry point
+bit for bit (FP32).  Correlator errors are the plain per-channel norm over
+t, ||C - C_ref|| / ||C_ref||, for both storages.  Fields are compared on
+timeslice 0, globally and per z-plane.  Over all timeslices, every float16
+job's correlators also stay within the reduced-precision bound of FP32's.
 """
+import os
+import tempfile
+
 import numpy as np
 import pytest
 import torch
 
-from oracle import hadron, smear
+from oracle import hadron
 from synth import configs
 from synth import device as synth_dev
-from tests.parity_util import TOL_BF16, TOL_F32, corr_err, field_err, proj_err
+from tests import oracle_pool
+from tests.parity_util import TOL_BF16, TOL_F32, corr_err, field_err, field_err_t
 
 pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 
@@ -64,23 +66,40 @@ def test_batch64_full_size_fp32_and_f16(qdpg_gpu):
             sample[d] = r
     assert len(sample) == 4
     report = {}
-    for d, r in sorted(sample.items()):
-        j = r["job"]
-        Ut = r["U_can"][:, 0:1].cpu().numpy().astype(np.complex128)
-        Pt = r["P_can"][0:1].cpu().numpy().astype(np.complex128)
-        ref = smear.gauss_smear(Ut, Pt, j["kappa"], j["n_iter"], 3)
-        C_ref = hadron.meson_2pt(ref, ref, hadron.SIXTEEN_MESONS)           # (16, 1, 1)
-        A = np.array([[np.abs(hadron.meson_site(ref, ref, a, b)).sum()] for a, b in hadron.SIXTEEN_MESONS])
-        e = {}
-        for tag in ("32", "h"):
-            got = r["p" + tag].export()[0:1].cpu().numpy()
-            C = r["m" + tag][:, None, 0:1].cpu().numpy()
-            e[tag] = (field_err(got, ref), corr_err(C, C_ref), proj_err(C, C_ref, A))
-        report[f"{d[0]}^3x{d[3]} N={j['n_iter']} kappa={j['kappa']:.3f}"] = e
-        # the batch runs the one-job path's per-site arithmetic: same bits
-        g = r["p32"].like().import_(r["P_can"])
-        q.gauss_smear(r["U32"], g, j["kappa"], j["n_iter"], 3, scratch=g.like())
-        assert torch.equal(g.export(), r["p32"].export()), d
+    pool = oracle_pool.pool()            # spawned: no CUDA state in the workers
+    tmp = tempfile.mkdtemp(prefix="qdpg_b64_")
+    try:
+        pending = {}
+        for d, r in sorted(sample.items()):
+            j = r["job"]
+            Up, Pp = os.path.join(tmp, f"U{d[0]}.npy"), os.path.join(tmp, f"P{d[0]}.npy")
+            np.save(Up, r["U_can"].cpu().numpy())
+            np.save(Pp, r["P_can"].cpu().numpy())
+            pending[d] = [pool.apply_async(oracle_pool.timeslice_chain,
+                                           (Up, Pp, t, j["kappa"], j["n_iter"], hadron.SIXTEEN_MESONS, t == 0))
+                          for t in range(d[3])]
+        for d, r in sorted(sample.items()):
+            j = r["job"]
+            parts = [a.get() for a in pending[d]]
+            C_ref = np.stack([c for c, _ in parts], axis=-1)[:, None, :]    # (16, 1, Nt)
+            ref = parts[0][1]                                                # smeared timeslice 0
+            e = {}
+            for tag in ("32", "h"):
+                got = r["p" + tag].export()[0:1].cpu().numpy()
+                C = r["m" + tag][:, None, :].cpu().numpy()
+                # fields on timeslice 0: global and worst z-plane; correlators: plain p = 0 norm over t
+                e[tag] = (field_err(got, ref), corr_err(C, C_ref), field_err_t(got[0], ref[0]))
+            report[f"{d[0]}^3x{d[3]} N={j['n_iter']} kappa={j['kappa']:.3f}"] = e
+            # the batch runs the one-job path's per-site arithmetic: same bits
+            g = r["p32"].like().import_(r["P_can"])
+            q.gauss_smear(r["U32"], g, j["kappa"], j["n_iter"], 3, scratch=g.like())
+            assert torch.equal(g.export(), r["p32"].export()), d
+    finally:
+        pool.terminate()
+        pool.join()
+        for f in os.listdir(tmp):
+            os.remove(os.path.join(tmp, f))
+        os.rmdir(tmp)
     # float16 against FP32 over all timeslices, every job
     def corr_err_t(a, b):
         return corr_err(a.cpu().numpy()[:, None, :], b.cpu().numpy()[:, None, :])
@@ -88,6 +107,8 @@ def test_batch64_full_size_fp32_and_f16(qdpg_gpu):
     worst = max(corr_err_t(r["mh"], r["m32"]) for r in rows)
     print(report, "float16 vs FP32 over t, max over jobs:", worst)
     for key, e in report.items():
-        assert e["32"][0] <= TOL_F32 and e["32"][1] <= TOL_F32, (key, e)
-        assert e["h"][0] <= 5e-3 and e["h"][2] <= 5e-3, (key, e)  # float16 storage: observed ~1e-3
+        assert max(e["32"]) <= TOL_F32, (key, e)
+        assert e["h"][0] <= 5e-3, (key, e)                # float16 storage: observed ~1e-3
+        assert e["h"][1] <= TOL_BF16, (key, e)            # plain p = 0 norm over t against the checker
+        assert e["h"][2] <= TOL_BF16, (key, e)            # worst z-plane of timeslice 0
     assert worst <= TOL_BF16

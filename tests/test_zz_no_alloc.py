@@ -6,9 +6,14 @@ they must avoid the implicit synchronisation of cudaMalloc/cudaFree).  Its
 ping-pong buffer is the library's 32 MiB static device array.  The test calls
 it through the C ABI twice in a row -- the second call finds the first call's
 data still in the shared array -- and compares each result with
-qdpg_gauss_smear given a caller-owned scratch field.
+qdpg_gauss_smear given a caller-owned scratch field.  It also checks that the
+calls allocate nothing: the library's own allocation counter, torch's
+caching allocator and the CUDA memory pool of the device stay unchanged.
+FP32 and BF16 storage are covered, and a smearing long enough (kappa = 0.3,
+N = 60) that the power-of-two rescaling runs through the static scratch.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -26,32 +31,62 @@ def _stream():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _field(q, lat, kind, canon):
-    f = q.Field(lat, kind, q.F32, device="cuda:0")
+def _field(q, lat, kind, canon, prec=None):
+    f = q.Field(lat, kind, q.F32 if prec is None else prec, device="cuda:0")
     return f.import_(torch.from_numpy(canon.astype(np.complex64)).to("cuda:0"))
 
 
-@pytest.mark.parametrize("kind,dims,n_iter", [("prop", (8, 8, 8, 16), 7), ("ferm", (16, 16, 16, 32), 6)])
-def test_noalloc_matches_allocating_entry_point(qdpg_gpu, kind, dims, n_iter):
+def _pool_used():
+    """Bytes in use in the device's default CUDA memory pool (stream-ordered allocations)."""
+    from cuda.bindings import runtime as rt
+
+    err, pool = rt.cudaDeviceGetDefaultMemPool(0)
+    assert err == rt.cudaError_t.cudaSuccess
+    err, used = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
+    assert err == rt.cudaError_t.cudaSuccess
+    return int(used)
+
+
+def _memory_state(q):
+    torch.cuda.synchronize()
+    try:
+        pool = _pool_used()
+    except ImportError:                          # cuda-bindings absent: the other two figures stand
+        pool = None
+    return q.device_alloc_count(), torch.cuda.memory_allocated(), pool
+
+
+@pytest.mark.parametrize("kind,prec,dims,n_iter,kappa", [
+    ("prop", "f32", (8, 8, 8, 16), 7, 0.21),
+    ("ferm", "f32", (16, 16, 16, 32), 6, 0.21),
+    ("prop", "bf16", (8, 8, 8, 16), 5, 0.21),
+    ("prop", "f32", (8, 8, 4, 8), 60, 0.3),      # growth bound > 40 bits: rescaled by 2^-31 every 21 hops
+])
+def test_noalloc_matches_allocating_entry_point(qdpg_gpu, kind, prec, dims, n_iter, kappa):
     q = qdpg_gpu
     lib = q.load()
     lat = q.Lattice(dims, 3)
     U = _field(q, lat, q.GAUGE, fields.round_to_f32(fields.gauge_field(dims, 21, kind="haar")))
     K = q.PROPAGATOR if kind == "prop" else q.FERMION
-    kappa = 0.21
+    P = q.PREC_NAMES[prec]
+    tol = TOL_F32 if prec == "f32" else 1e-6      # BF16: both runs round identically; allow rounding-order slack
     for call, fid in enumerate((71, 72)):        # two calls in a row share the static scratch
         if kind == "prop":
             psi = fields.round_to_f32(fields.propagator(dims, 21, field_id=fid, envelope=0.3))
         else:
             psi = fields.round_to_f32(fields.fermion(dims, 21, field_id=fid))
-        ref = _field(q, lat, K, psi)
-        q.gauss_smear(U, ref, kappa, n_iter + call, 3, scratch=ref.like())
-        got = _field(q, lat, K, psi)
+        ref = _field(q, lat, K, psi, P)
+        scratch = ref.like()
+        q.gauss_smear(U, ref, kappa, n_iter + call, 3, scratch=scratch)
+        got = _field(q, lat, K, psi, P)
+        gc.collect()                             # no tensor of this test is freed inside the window below
+        before = _memory_state(q)
         rc = lib.qdpg_gauss_smear_noalloc(U._h, got._h, kappa, n_iter + call, 3, _stream())
         assert rc == 0
+        assert _memory_state(q) == before, "the allocation-free entry point allocated device memory"
         a = got.export().cpu().numpy()
         b = ref.export().cpu().numpy()
-        assert field_err(a, b) <= TOL_F32, call
+        assert field_err(a, b) <= tol, call
 
 
 def test_noalloc_rejects_a_field_beyond_the_static_scratch(qdpg_gpu):
