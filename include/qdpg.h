@@ -166,6 +166,9 @@ int qdpg_device_status(void* stream);
  *                              (the calls return QDPG_ERR_NOMEM); 0 = none;
  *  QDPG_DEBUG_STAGE_BYTES      largest chunk (bytes of canonical data, at least one
  *                              timeslice) of the host-buffer import/export; 0 = 256 MiB;
+ *  QDPG_DEBUG_MESON_UNSTAGED   1: F32/BF16 meson contractions read S2 from global memory
+ *                              for every mask pair instead of staging it in shared
+ *                              memory (the two give the same values); 0 = staged;
  * and launch-shape settings of the pipelined smearing kernel:
  *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..288, 0 = default;
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
@@ -185,15 +188,21 @@ enum {
   QDPG_TUNE_F16_WARPS = 8,
   QDPG_TUNE_TENSOR_COPY = 9,
   QDPG_DEBUG_FAIL_ALLOCS = 11,
-  QDPG_DEBUG_STAGE_BYTES = 12
+  QDPG_DEBUG_STAGE_BYTES = 12,
+  QDPG_DEBUG_MESON_UNSTAGED = 13
 };
 int qdpg_debug_set(int what, long long value);
 
 /* Device allocations the library has made for its own temporaries in this
  * process (smearing scratch when none is given, site values of the momentum
  * projection, staging buffers of the host-buffer import/export).  All are
- * stream-ordered (cudaMallocAsync) and freed on the same stream. */
+ * stream-ordered, from the library's own memory pool on each device
+ * (cudaMallocFromPoolAsync; created on first use, it keeps up to 4 GiB of
+ * freed memory mapped for the next call), and freed on the same stream.
+ * qdpg_device_pool_used reports the bytes of that pool in use on the current
+ * device. */
 uint64_t qdpg_device_alloc_count(void);
+int qdpg_device_pool_used(uint64_t* bytes);
 
 /* ---- autotuning of the smearing kernel --------------------------------------
  * The pipelined smearing kernel's tile width and grid (persistent or one CTA
@@ -254,7 +263,7 @@ int qdpg_field_export(qdpg_field_t src, double* canon_dev, void* stream);
  * above (import: complex double or complex float per `canon`; export:
  * complex double).  Same conversions as qdpg_field_import/export.
  *  - The data moves through a device staging buffer that the library
- *    allocates stream-ordered (cudaMallocAsync) and frees on `stream` after
+ *    allocates stream-ordered (the library's pool, see below) and frees on `stream` after
  *    the last chunk: one cudaMemcpyAsync per contiguous run of whole
  *    timeslices (at most 256 MiB of canonical data per chunk) when
  *    j_decay = 3, where a timeslice is contiguous in the canonical order

@@ -68,6 +68,7 @@ def load() -> ctypes.CDLL:
         "qdpg_field_import_host": (i, [vp, vp, i, vp]),
         "qdpg_field_export_host": (i, [vp, vp, vp]),
         "qdpg_device_alloc_count": (ctypes.c_uint64, []),
+        "qdpg_device_pool_used": (i, [ctypes.POINTER(ctypes.c_uint64)]),
         "qdpg_point_source": (i, [vp, ip, i, vp]),
         "qdpg_shift": (i, [vp, vp, i, i, vp]),
         "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
@@ -123,13 +124,20 @@ def launch_count() -> int:
 
 
 DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_STAGE, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
-DEBUG_FAIL_ALLOCS, DEBUG_STAGE_BYTES = 11, 12
+DEBUG_FAIL_ALLOCS, DEBUG_STAGE_BYTES, DEBUG_MESON_UNSTAGED = 11, 12, 13
 TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_GRID, TUNE_TENSOR_COPY = 4, 5, 7, 9
 
 
 def device_alloc_count() -> int:
     """Device allocations libqdpg has made for its own temporaries in this process."""
     return int(load().qdpg_device_alloc_count())
+
+
+def device_pool_used() -> int:
+    """Bytes in use in libqdpg's own device memory pool on the current device."""
+    v = ctypes.c_uint64()
+    _check(load().qdpg_device_pool_used(ctypes.byref(v)))
+    return int(v.value)
 
 
 def device_status(stream=None):

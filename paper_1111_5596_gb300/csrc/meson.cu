@@ -23,12 +23,15 @@
 // atomic per block and value.
 #include <cuda_fp16.h>
 
+#include <cstring>
 #include <type_traits>
 #include <vector>
 
+#include "gamma_host.h"
+#include "ptx.cuh"
 #include "qdpg_internal.h"
 #include "qdpg_profile.h"
-#include "gamma_host.h"
+#include "tmap.h"
 
 namespace qdpg {
 
@@ -47,6 +50,9 @@ struct MesonPass {
   int q_of[kMaxPassCh];          // pair index of each channel
   int out_row[kMaxPassCh];       // channel index in the output
   float2 w[kMaxPassCh][16];      // weight of Q_q[alpha*4 + beta]
+  int jlo[4], jhi[4];            // channels of pair q: jlo[q] <= j < jhi[q] (grouped by pair)
+  unsigned long long wre[kMaxPassCh][16];  // (w.x, w.x) and (w.y, w.y) as packed FP32 pairs
+  unsigned long long wim[kMaxPassCh][16];
 };
 
 struct Moms {
@@ -57,6 +63,30 @@ struct Moms {
 };
 
 __device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
+typedef unsigned long long u64;
+__device__ __forceinline__ u64 pack2(float x, float y) {
+  u64 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
+  return r;
+}
+__device__ __forceinline__ float2 unpack2(u64 r) {
+  float2 v;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
+  return v;
+}
+// d = a (.) b + c, two FP32 lanes, round to nearest
+__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
+  u64 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ u64 lds_pair_st(const float2* p) { return *reinterpret_cast<const u64*>(p); }
+__device__ __forceinline__ u64 lds_pair_st(const __nv_bfloat162* p) {
+  const float2 v = __bfloat1622float2(*p);
+  return pack2(v.x, v.y);
+}
+__device__ __forceinline__ float2 lds_elem(const float2* p) { return *p; }
+__device__ __forceinline__ float2 lds_elem(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
 __device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
   __nv_bfloat162 v = *p;
   return __bfloat1622float2(v);
@@ -115,6 +145,16 @@ __device__ __forceinline__ void stage_f16(uint32_t* dst, const __half2* S, int t
       d[3] = v.w;
     }
   }
+}
+
+// s + e = a + b exactly (Knuth's TwoSum, six FP32 additions; the compiler
+// must not reassociate them, which CUDA does not do without fast-math).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  const float x = __fadd_rn(a, b);
+  const float bv = __fsub_rn(x, a);
+  const float av = __fsub_rn(x, bv);
+  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+  s = x;
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -262,14 +302,326 @@ __global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __rest
   }
 }
 
+
+// ---- staged kernel (component-major F32 / BF16 propagators) -----------------
+//
+// A block owns kStSites consecutive sites of one timeslice.  S2, which every
+// mask pair re-reads, is staged once in shared memory by one tensor-map copy
+// (box: the block's sites x the 144 components, [comp][site] in shared
+// memory, so a warp's 32 sites of one component are 256 consecutive bytes);
+// S1 is read once per element (from the staged copy when S1 = S2).  Two
+// threads share a site: thread half h forms the colour contractions of sink
+// spins 2h and 2h+1, and the channel values, linear in Q, are sums of the
+// two halves' partial values (added in the timeslice sums, or through shared
+// memory for site values).
+constexpr int kStSites = 64;
+constexpr int kStThreads = 2 * kStSites;
+
+template <int NQ, typename PsiT, bool SITES, bool SAME>
+__global__ void __launch_bounds__(kStThreads) meson_staged_kernel(const __grid_constant__ CUtensorMap map2,
+                                                                  const PsiT* __restrict__ S1, Geom g, MesonPass P,
+                                                                  Moms M, double* __restrict__ out,
+                                                                  float2* __restrict__ sites, const ScaleRecord* rec1,
+                                                                  const ScaleRecord* rec2, int site_scale,
+                                                                  double2* __restrict__ partial, unsigned int* status,
+                                                                  long long timeout_ns) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  PsiT* st = reinterpret_cast<PsiT*>(smem_raw);                         // [144][kStSites]
+  constexpr uint32_t kStageBytes = 144u * kStSites * sizeof(PsiT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + kStageBytes);
+  float2* cval = reinterpret_cast<float2*>(smem_raw + kStageBytes + 16);   // [nch][kStSites] channel values
+  float2* phase = cval + kMaxPassCh * kStSites;                           // [n_mom][kStSites] cos, sin
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int site = tid & (kStSites - 1), h = tid / kStSites;
+  const int s0 = blockIdx.x * kStSites, t = blockIdx.y;
+  const int s3 = s0 + site;
+  const bool live = s3 < g.V3;
+  const int V3 = g.V3;
+  const uint32_t bar_a = ptx::smem_addr(bar);
+
+  if (tid == 0) {
+    ptx::mbar_init(bar_a, 1);
+    ptx::fence_mbar_init();
+    ptx::mbar_arrive_expect_tx(bar_a, kStageBytes);
+    ptx::tensor_g2s_2d(ptx::smem_addr(st), &map2, s0, t * 144, bar_a);
+  }
+  __syncthreads();
+  const bool ok = ptx::mbar_wait_bounded(bar_a, 0, timeout_ns);
+  if (!__syncthreads_and(ok ? 1 : 0)) {
+    // the copy did not complete in time: record it, give the copy one more
+    // bounded wait so that it is not in flight when the block exits
+    if (tid == 0) {
+      atomicOr(status, kStatusFullWait);
+      if (!ptx::mbar_wait_bounded(bar_a, 0, timeout_ns)) atomicOr(status, kStatusDrain);
+    }
+    return;
+  }
+
+  const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
+  const PsiT* s1g = S1 + (long long)t * 144 * V3 + s3;
+  auto p1 = [&](int comp) -> float2 {
+    if constexpr (SAME) return lds_elem(st + comp * kStSites + site);
+    else return ld2(s1g + (long long)comp * V3);
+  };
+  auto p2 = [&](int comp) -> float2 { return lds_elem(st + comp * kStSites + site); };
+
+  // Q_q(alpha, beta) for alpha = 2h + i (index i*4 + beta) as packed pairs:
+  // with x = S1 element and y = S2 element, x conj(y) = (P.x + P.y, R.x + R.y)
+  // for P = (x.x, x.y) (.) y and R = (x.y, -x.x) (.) y: two fma.rn.f32x2 per
+  // complex multiply-accumulate, y used as loaded.
+  u64 Qp[NQ][8], Qr[NQ][8];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int be = 0; be < 4; ++be) {
+      const int al = 2 * h + i;
+      u64 xa[9], xr[9];
+#pragma unroll
+      for (int d = 0; d < 3; ++d)
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+          const float2 x = live ? p1((al * 3 + d) * 12 + be * 3 + b) : make_float2(0.f, 0.f);
+          xa[d * 3 + b] = pack2(x.x, x.y);
+          xr[d * 3 + b] = pack2(x.y, -x.x);
+        }
+#pragma unroll
+      for (int q = 0; q < NQ; ++q) {
+        const int base = ((al ^ P.ma[q]) * 3) * 12 + (be ^ P.mb[q]) * 3;
+        u64 pa = 0ull, ra = 0ull;
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            const u64 y = live ? lds_pair_st(st + (base + d * 12 + b) * kStSites + site) : 0ull;
+            pa = fma2(xa[d * 3 + b], y, pa);
+            ra = fma2(xr[d * 3 + b], y, ra);
+          }
+        Qp[q][i * 4 + be] = pa;
+        Qr[q][i * 4 + be] = ra;
+      }
+    }
+  // Q as (re, im) pairs and i Q = (-im, re), for the weighted channel sums
+  u64 Qz[NQ][8], Qi[NQ][8];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float2 a = unpack2(Qp[q][k]), b = unpack2(Qr[q][k]);
+      const float re = a.x + a.y, im = b.x + b.y;
+      Qz[q][k] = pack2(re, im);
+      Qi[q][k] = pack2(-im, re);
+    }
+  // this half's part of channel j: sum_k (w.x, w.x) (.) Q + (w.y, w.y) (.) iQ
+  auto part_of = [&](int q, int j) -> float2 {
+    u64 c = 0ull;
+    for (int qq = 0; qq < NQ; ++qq) {
+      if (qq != q) continue;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        c = fma2(P.wre[j][8 * h + k], Qz[qq][k], c);
+        c = fma2(P.wim[j][8 * h + k], Qi[qq][k], c);
+      }
+    }
+    return unpack2(c);
+  };
+  // the upper half's parts go through shared memory; the lower half adds its
+  // own and stores the channel value (cval[j][site], or the site output)
+  if (h == 1) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      for (int j = P.jlo[q]; j < P.jhi[q]; ++j) cval[j * kStSites + site] = part_of(q, j);
+  }
+  __syncthreads();
+  if (h == 0) {
+#pragma unroll
+    for (int q = 0; q < NQ; ++q)
+      for (int j = P.jlo[q]; j < P.jhi[q]; ++j) {
+        const float2 mine = part_of(q, j), o = cval[j * kStSites + site];
+        const float2 c = live ? make_float2(mine.x + o.x, mine.y + o.y) : make_float2(0.f, 0.f);
+        if constexpr (SITES) {
+          if (live)
+            sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] =
+                (scale_exp && site_scale) ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
+        } else {
+          cval[j * kStSites + site] = c;
+        }
+      }
+  } else if (!SITES && !M.zero_only) {
+    // phases exp(-i p.(x - x0)) of the block's sites, one momentum per pass of the upper half
+    int c0 = 0, c1 = 0, c2 = 0;
+    if (live) {
+      c0 = s3 % g.sL[0];
+      c1 = (s3 / g.sL[0]) % g.sL[1];
+      c2 = s3 / (g.sL[0] * g.sL[1]);
+    }
+    for (int m = 0; m < M.n; ++m) {
+      // phase index: sum_k n_k (x_k - o_k) V3/L_k  (mod V3), exact in integers
+      long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
+                      (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
+                      (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
+      num %= V3;
+      if (num < 0) num += V3;
+      float sn, cs;
+      sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
+      phase[m * kStSites + site] = make_float2(cs, sn);
+    }
+  }
+  if constexpr (SITES) return;
+  __syncthreads();
+  // sums over the block's sites of c_j(x) exp(-i p_m.(x - x0)): warp w takes
+  // values w, w + 4, ...; each lane adds two sites, then a butterfly in
+  // two-float arithmetic (hi + lo, error-free sums), FP64 only for the
+  // block's one atomic per value
+  const int nv = P.nch * M.n;
+  for (int v = warp; v < nv; v += kStThreads / 32) {
+    const int j = v / M.n, m = v % M.n;
+    float2 a = cval[j * kStSites + lane], b = cval[j * kStSites + lane + 32];
+    if (!M.zero_only) {
+      const float2 pa = phase[m * kStSites + lane], pb = phase[m * kStSites + lane + 32];
+      a = make_float2(a.x * pa.x + a.y * pa.y, a.y * pa.x - a.x * pa.y);  // c (cs - i sn)
+      b = make_float2(b.x * pb.x + b.y * pb.y, b.y * pb.x - b.x * pb.y);
+    }
+    float2 hi, lo;
+    two_sum(a.x, b.x, hi.x, lo.x);
+    two_sum(a.y, b.y, hi.y, lo.y);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float hx = __shfl_xor_sync(0xffffffffu, hi.x, o), lx = __shfl_xor_sync(0xffffffffu, lo.x, o);
+      const float hy = __shfl_xor_sync(0xffffffffu, hi.y, o), ly = __shfl_xor_sync(0xffffffffu, lo.y, o);
+      float ex, ey;
+      two_sum(hi.x, hx, hi.x, ex);
+      two_sum(hi.y, hy, hi.y, ey);
+      lo.x = lo.x + lx + ex;
+      lo.y = lo.y + ly + ey;
+    }
+    if (lane == 0)  // this block's part of the sum; meson_fold_kernel adds the blocks in order
+      partial[((long long)t * gridDim.x + blockIdx.x) * nv + v] = make_double2((double)hi.x + (double)lo.x,
+                                                                               (double)hi.y + (double)lo.y);
+  }
+}
+
+// out[value][t] = 2^exp * sum over the blocks of timeslice t of their partial
+// sums (fixed order: the result does not depend on scheduling).
+__global__ void __launch_bounds__(128) meson_fold_kernel(const double2* __restrict__ partial, int nbx, MesonPass P,
+                                                         int n_mom, int Nt, double* __restrict__ out,
+                                                         const ScaleRecord* rec1, const ScaleRecord* rec2) {
+  __shared__ double2 red[4];
+  const int v = blockIdx.x, t = blockIdx.y, nv = P.nch * n_mom;
+  double re = 0.0, im = 0.0;
+  for (int b = threadIdx.x; b < nbx; b += 128) {
+    const double2 x = partial[((long long)t * nbx + b) * nv + v];
+    re += x.x;
+    im += x.y;
+  }
+  re = warp_sum(re);
+  im = warp_sum(im);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_double2(re, im);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    re = red[0].x + red[1].x + red[2].x + red[3].x;
+    im = red[0].y + red[1].y + red[2].y + red[3].y;
+    const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
+    const int j = v / n_mom, m = v % n_mom;
+    const long long o = ((long long)P.out_row[j] * n_mom + m) * Nt + t;
+    out[2 * o] = ldexp(re, scale_exp);
+    out[2 * o + 1] = ldexp(im, scale_exp);
+  }
+}
+
+// The staged kernel for one pass, or QDPG_ERR_UNSUPPORTED where it does not
+// apply (float16's site-major layout; a component row of the timeslice not a
+// multiple of 16 bytes; no tensor-map support).
+int launch_staged_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
+                       float2* sites, cudaStream_t s, int site_scale) {
+  const Geom& g = S1->g;
+  const bool bf = S1->prec == QDPG_BF16;
+  if (S1->prec != QDPG_F32 && !bf) return QDPG_ERR_UNSUPPORTED;
+  const int esize = bf ? 4 : 8;
+  if (((long long)g.V3 * esize) % 16 != 0 || reinterpret_cast<uintptr_t>(S2->data) % 16 != 0) return QDPG_ERR_UNSUPPORTED;
+  CUtensorMap map;
+  if (!encode_map_2d(&map, S2->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144, (uint64_t)g.V3 * esize, kStSites,
+                     144))
+    return QDPG_ERR_UNSUPPORTED;
+  unsigned int* status = device_status_word();
+  if (!status) return QDPG_ERR_UNSUPPORTED;
+  const bool same = S1->data == S2->data;
+  const size_t stage = (size_t)144 * kStSites * esize;
+  const size_t smem = stage + 16 + (size_t)(kMaxPassCh + M.n) * kStSites * sizeof(float2);
+  dim3 grid((g.V3 + kStSites - 1) / kStSites, g.Nt);
+  // per-block partial sums of the timeslice/momentum values (no atomics:
+  // hundreds of blocks per timeslice would serialise on the same outputs)
+  void* partial = nullptr;
+  if (!sites) {
+    const int arc = dev_alloc(&partial, sizeof(double2) * (size_t)grid.x * g.Nt * P.nch * M.n, s,
+                              "meson_2pt partial sums");
+    if (arc != QDPG_OK) return arc;
+  }
+  ProfScope prof("meson_2pt", s);
+  cudaError_t e = cudaSuccess;
+#define QDPG_STAGED(NQ, T, SITES, SAME)                                                                        \
+  do {                                                                                                         \
+    auto k = meson_staged_kernel<NQ, T, SITES, SAME>;                                                          \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+    if (e == cudaSuccess)                                                                                      \
+      k<<<grid, kStThreads, smem, s>>>(map, static_cast<const T*>(S1->data), g, P, M, out, sites, S1->rec,     \
+                                       S2->rec, site_scale, static_cast<double2*>(partial), status,            \
+                                       wait_timeout_ns());                                                     \
+  } while (0)
+#define QDPG_STAGED_T(NQ, T)                                  \
+  do {                                                        \
+    if (sites && same) QDPG_STAGED(NQ, T, true, true);        \
+    else if (sites) QDPG_STAGED(NQ, T, true, false);          \
+    else if (same) QDPG_STAGED(NQ, T, false, true);           \
+    else QDPG_STAGED(NQ, T, false, false);                    \
+  } while (0)
+#define QDPG_STAGED_NQ(NQ)                                    \
+  do {                                                        \
+    if (bf) QDPG_STAGED_T(NQ, __nv_bfloat162);                \
+    else QDPG_STAGED_T(NQ, float2);                           \
+  } while (0)
+  switch (P.nq) {
+    case 1: QDPG_STAGED_NQ(1); break;
+    case 2: QDPG_STAGED_NQ(2); break;
+    case 3: QDPG_STAGED_NQ(3); break;
+    default: QDPG_STAGED_NQ(4); break;
+  }
+#undef QDPG_STAGED_NQ
+#undef QDPG_STAGED_T
+#undef QDPG_STAGED
+  if (e != cudaSuccess) {
+    dev_free(partial, s);
+    return fail(QDPG_ERR_CUDA, "meson_2pt: smem attribute: %s", cudaGetErrorString(e));
+  }
+  int rc = check_launch("meson_2pt");
+  if (rc == QDPG_OK && !sites) {
+    meson_fold_kernel<<<dim3(P.nch * M.n, g.Nt), 128, 0, s>>>(static_cast<const double2*>(partial), (int)grid.x, P,
+                                                              M.n, g.Nt, out, S1->rec, S2->rec);
+    rc = check_launch("meson_2pt fold");
+  }
+  dev_free(partial, s);
+  return rc;
+}
+
 struct Channel {
   int row, ma, mb;
   float2 w[16];
 };
 
+// (lo, hi) FP32 pair as the 64-bit register image fma.rn.f32x2 takes (lo in the low word).
+inline unsigned long long pack_host(float lo, float hi) {
+  unsigned int a, b;
+  memcpy(&a, &lo, 4);
+  memcpy(&b, &hi, 4);
+  return (unsigned long long)a | ((unsigned long long)b << 32);
+}
+
 int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
                 float2* sites, cudaStream_t s, int site_scale = 1) {
   const Geom& g = S1->g;
+  if (!debug_meson_unstaged()) {
+    const int rc = launch_staged_pass(P, M, S1, S2, out, sites, s, site_scale);
+    if (rc != QDPG_ERR_UNSUPPORTED) return rc;
+  }
   dim3 grid((g.V3 + kMesonThreads - 1) / kMesonThreads, g.Nt);
   size_t smem = sites ? 0 : (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
   const bool bf = S1->prec == QDPG_BF16;
@@ -431,8 +783,15 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
     }
     P.q_of[P.nch] = q;
     P.out_row[P.nch] = c.row;
-    for (int k = 0; k < 16; ++k) P.w[P.nch][k] = c.w[k];
+    for (int k = 0; k < 16; ++k) {
+      P.w[P.nch][k] = c.w[k];
+      P.wre[P.nch][k] = pack_host(c.w[k].x, c.w[k].x);
+      P.wim[P.nch][k] = pack_host(c.w[k].y, c.w[k].y);
+    }
     ++P.nch;
+    // channels arrive grouped by mask pair, so pair q's channels are contiguous
+    if (P.jhi[q] == 0) P.jlo[q] = P.nch - 1;
+    P.jhi[q] = P.nch;
   }
   return flush();
 }

@@ -9,15 +9,25 @@
 //   B[2x][2m] = cos,  B[2x+1][2m] = sin,  B[2x][2m+1] = -sin,  B[2x+1][2m+1] = cos
 // for exp(-i theta) = cos - i sin, so that C[row][2m] = Re and C[row][2m+1] = Im.
 //
-// Each CTA owns 128 rows and a range of sites.  It stages 32 sites at a time
-// in shared memory in the tensor cores' K-major core-matrix layout (8 rows x
-// 16 bytes per core matrix), the phases generated on the fly, and one thread
+// A CTA owns 128 rows and at most kMaxCtaSites sites, in chunks of kChunk
+// sites staged in shared memory (two buffers: the threads stage chunk c + 1
+// while the tensor cores work on chunk c) in the K-major core-matrix layout
+// (8 rows x 16 bytes per core matrix).  Site values arrive as 16-byte loads
+// (two sites of one row), the next chunk's loads in flight while the current
+// chunk is split and stored, and each warp's stores fill whole 512-byte runs,
+// so staging has no bank conflicts.  The phase operand is the same for every
+// row tile: a first kernel writes it for all sites, already split into hi +
+// lo in the shared-memory image of each chunk, and one bulk copy per chunk
+// brings it in.  The phases are products of three per-direction tables,
+// exp(-2 pi i j / L_k), so no angle is reduced per site.  One thread
 // issues tcgen05.mma (kind::tf32, M = 128, N = 2*n_mom padded to 16) into a
-// TMEM accumulator.  TF32 keeps 10 mantissa bits, so every operand is split
+// TMEM accumulator; TF32 keeps 10 mantissa bits, so every operand is split
 // into hi + lo parts and three products hi*hi + hi*lo + lo*hi are
-// accumulated (relative error ~2^-21 per product).  The CTA's FP32 partial
-// sum over its sites is read back with tcgen05.ld and added to the FP64
-// output with atomics (FP64 only for the sums across CTAs).
+// accumulated (relative error ~2^-21 per product).  The CTA's FP32 sum over
+// its sites (the accumulator depth, at most kMaxCtaSites, bounds its
+// rounding) goes to a buffer of partial sums; a last kernel adds the CTAs'
+// partial sums in a fixed order in two-float arithmetic (error-free FP32
+// sums, FP64 once per output) and applies the fields' scale.
 #include <algorithm>
 
 #include "ptx.cuh"
@@ -28,64 +38,107 @@ namespace qdpg {
 
 namespace {
 
-constexpr int kM = 128;            // rows per CTA (tensor-core M)
-constexpr int kChunk = 32;         // sites per staged chunk
-constexpr int kKt = 2 * kChunk;    // real K per chunk
-constexpr int kMaxMomP = 64;       // N = 2*n_mom <= 128
-constexpr int kTmemCols = 128;
-constexpr int kMaxAccSites = 256;  // sites summed in one FP32 tensor-core accumulator
+constexpr int kM = 128;             // rows per CTA (tensor-core M)
+constexpr int kChunk = 16;          // sites per staged chunk
+constexpr int kKt = 2 * kChunk;     // real K per chunk
+constexpr int kMaxMomP = 64;        // N = 2*n_mom <= 128
+constexpr int kMaxCtaSites = 576;   // sites summed in one FP32 tensor-core accumulator
+constexpr int kMaxL = 128;          // longest spatial extent of the phase tables
 
 struct ProjArgs {
-  const ScaleRecord* ra;  // optional field scales: the sums are multiplied by
-  const ScaleRecord* rb;  // 2^(ca * ra->exp + cb * rb->exp) (null: 2^0)
-  int ca, cb;
   int rows;           // n_chan * Nt
-  int Nt, V3, nmom, npad, sites_per_cta;
+  int Nt, V3, nmom, npad;
+  int sites_per_cta;  // multiple of kChunk
   int sL[3];
   int origin[3];
   int k[kMaxMomP][3];
 };
 
-// byte offset of element (r, k) of a K-major tile with kKt columns
-__device__ __forceinline__ uint32_t core_off(int r, int k) {
-  return (uint32_t)(((r >> 3) * (kKt / 4) + (k >> 2)) * 128 + (r & 7) * 16 + (k & 3) * 4);
+// Byte offset of the core-matrix row holding k = 4*kc .. 4*kc+3 of row r in
+// a K-major tile of kKt columns.
+__device__ __forceinline__ uint32_t core_row(int r, int kc) {
+  return (uint32_t)(((r >> 3) * (kKt / 4) + kc) * 128 + (r & 7) * 16);
 }
 
-__device__ __forceinline__ void split_tf32(float v, float& hi, float& lo) {
-  hi = __uint_as_float(__float_as_uint(v) & 0xFFFFE000u);
-  lo = v - hi;
+__device__ __forceinline__ void split4(float4 v, float4& hi, float4& lo) {
+  auto h = [](float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); };
+  hi = make_float4(h(v.x), h(v.y), h(v.z), h(v.w));
+  lo = make_float4(v.x - hi.x, v.y - hi.y, v.z - hi.z, v.w - hi.w);
 }
 
-__device__ __forceinline__ void put(unsigned char* hi_base, unsigned char* lo_base, int r, int k, float v) {
-  float h, l;
-  split_tf32(v, h, l);
-  const uint32_t o = core_off(r, k);
-  *reinterpret_cast<float*>(hi_base + o) = h;
-  *reinterpret_cast<float*>(lo_base + o) = l;
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-__global__ void __launch_bounds__(128, 1) momproj_kernel(const float2* __restrict__ sites, ProjArgs P,
-                                                         double* __restrict__ out, unsigned int* status,
-                                                         long long timeout_ns) {
+// The phase operand of every chunk, in its shared-memory image: for chunk c,
+// [hi | lo] x (npad rows x kKt K-major core matrices); rows 2m: (cos, sin),
+// rows 2m+1: (-sin, cos) per site, zero beyond V3 and for the padding rows.
+__global__ void __launch_bounds__(256) phase_tile_kernel(ProjArgs P, float4* __restrict__ tiles) {
+  __shared__ float2 tab[3][kMaxL];  // exp(-2 pi i j / L_k)
+  for (int i = threadIdx.x; i < 3 * kMaxL; i += 256) {
+    const int k = i / kMaxL, j = i % kMaxL;
+    float sn = 0.f, cs = 1.f;
+    if (j < P.sL[k]) sincospif(2.0f * (float)j / (float)P.sL[k], &sn, &cs);
+    tab[k][j] = make_float2(cs, -sn);
+  }
+  __syncthreads();
+  // one thread per (chunk, row n, core-matrix column kc): two sites, one row
+  const int per_chunk = P.npad * (kKt / 4);
+  const long long total = (long long)((P.V3 + kChunk - 1) / kChunk) * per_chunk;
+  for (long long i = blockIdx.x * 256LL + threadIdx.x; i < total; i += (long long)gridDim.x * 256) {
+    const int c = (int)(i / per_chunk), rem = (int)(i % per_chunk);
+    const int n = rem / (kKt / 4), kc = rem % (kKt / 4), m = n >> 1;
+    float2 ph[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+    if (m < P.nmom) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int xs = c * kChunk + 2 * kc + e;
+        if (xs < P.V3) {
+          const int cc[3] = {xs % P.sL[0], (xs / P.sL[0]) % P.sL[1], xs / (P.sL[0] * P.sL[1])};
+          float2 f = make_float2(1.f, 0.f);
+#pragma unroll
+          for (int k = 0; k < 3; ++k) {
+            const int L = P.sL[k];
+            const int d = ((cc[k] - P.origin[k]) % L + L) % L;
+            const int j = ((P.k[m][k] * d) % L + L) % L;
+            f = cmulf(f, tab[k][j]);
+          }
+          ph[e] = f;  // exp(-i p.(x - x0)) = (cos, -sin)
+        }
+      }
+    }
+    const float4 v = (n & 1) ? make_float4(ph[0].y, ph[0].x, ph[1].y, ph[1].x)
+                             : make_float4(ph[0].x, -ph[0].y, ph[1].x, -ph[1].y);
+    float4 hi, lo;
+    split4(v, hi, lo);
+    const size_t base = (size_t)c * 2 * per_chunk;  // float4 units: [hi tile][lo tile]
+    const size_t o = core_row(n, kc) / 16;
+    tiles[base + o] = hi;
+    tiles[base + per_chunk + o] = lo;
+  }
+}
+
+__global__ void __launch_bounds__(128) momproj_kernel(const float2* __restrict__ sites, ProjArgs P,
+                                                      const float4* __restrict__ tiles, float* __restrict__ partial,
+                                                      unsigned int* status, long long timeout_ns) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  unsigned char* Ahi = smem;
-  unsigned char* Alo = Ahi + kM * kKt * 4;
-  unsigned char* Bhi = Alo + kM * kKt * 4;
-  unsigned char* Blo = Bhi + P.npad * kKt * 4;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(Blo + P.npad * kKt * 4);
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 1);
+  const uint32_t a_bytes = kM * kKt * 4, b_bytes = P.npad * kKt * 4;
+  const uint32_t stage_bytes = 2 * a_bytes + 2 * b_bytes;  // A hi, A lo, B hi, B lo
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * stage_bytes);  // [2] tensor cores done, [2] B landed
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 4);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row0 = blockIdx.x * kM;
   const int xb = blockIdx.y * P.sites_per_cta;
   const int xe = min(P.V3, xb + P.sites_per_cta);
-  const uint32_t bar_a = ptx::smem_addr(bar);
+  const int nchunks = (xe - xb + kChunk - 1) / kChunk;
+  const int tcols = P.npad <= 32 ? 32 : (P.npad <= 64 ? 64 : 128);
 
   if (warp == 0) {
-    ptx::tmem_alloc(ptx::smem_addr(tslot), kTmemCols);
+    ptx::tmem_alloc(ptx::smem_addr(tslot), tcols);
     ptx::tmem_relinquish();
   }
   if (tid == 0) {
-    ptx::mbar_init(bar_a, 1);
+    for (int i = 0; i < 4; ++i) ptx::mbar_init(ptx::smem_addr(bar + i), 1);
     ptx::fence_mbar_init();
   }
   ptx::tc_fence_before();
@@ -94,94 +147,182 @@ __global__ void __launch_bounds__(128, 1) momproj_kernel(const float2* __restric
   const uint32_t tmem = *tslot;
   const uint32_t idesc = ptx::idesc_tf32(kM, P.npad);
 
-  uint32_t phase = 0;
-  bool issued = false, ok = true;
-  for (int x0 = xb; x0 < xe && ok; x0 += kChunk) {
-    // A: 128 rows x 32 sites (complex) -> real K = 64
-    for (int e = tid; e < kM * kChunk; e += blockDim.x) {
-      const int r = e / kChunk, j = e % kChunk;
-      const int row = row0 + r, x = x0 + j;
-      float2 v = make_float2(0.f, 0.f);
-      if (row < P.rows && x < xe) v = __ldg(sites + (size_t)row * P.V3 + x);
-      put(Ahi, Alo, r, 2 * j, v.x);
-      put(Ahi, Alo, r, 2 * j + 1, v.y);
-    }
-    // B: npad rows (2 per momentum) x real K = 64
-    for (int e = tid; e < (P.npad / 2) * kChunk; e += blockDim.x) {
-      const int m = e / kChunk, j = e % kChunk;
-      const int x = x0 + j;
-      float cs = 0.f, sn = 0.f;
-      if (m < P.nmom && x < xe) {
-        const int c0 = x % P.sL[0], c1 = (x / P.sL[0]) % P.sL[1], c2 = x / (P.sL[0] * P.sL[1]);
-        long long num = (long long)P.k[m][0] * (((c0 - P.origin[0]) % P.sL[0] + P.sL[0]) % P.sL[0]) * (P.V3 / P.sL[0]) +
-                        (long long)P.k[m][1] * (((c1 - P.origin[1]) % P.sL[1] + P.sL[1]) % P.sL[1]) * (P.V3 / P.sL[1]) +
-                        (long long)P.k[m][2] * (((c2 - P.origin[2]) % P.sL[2] + P.sL[2]) % P.sL[2]) * (P.V3 / P.sL[2]);
-        num %= P.V3;
-        if (num < 0) num += P.V3;
-        sincospif(2.0f * (float)num / (float)P.V3, &sn, &cs);
+  // A of one chunk: this thread's 8 core-matrix rows (two sites each)
+  constexpr int kAPer = (kM / 8) * (kKt / 4) / 4 / 4;  // warp tasks per warp
+  float4 va[kAPer];
+  auto load_a = [&](int c) {
+    const int x0 = xb + c * kChunk;
+#pragma unroll
+    for (int i = 0; i < kAPer; ++i) {
+      const int u = warp + 4 * i;
+      const int rg = u / (kKt / 16), kc = (u % (kKt / 16)) * 4 + (lane >> 3);
+      const int row = row0 + rg * 8 + (lane & 7), x = x0 + 2 * kc;
+      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (row < P.rows) {
+        const float2* src = sites + (size_t)row * P.V3 + x;
+        if (x + 1 < xe && ((reinterpret_cast<uintptr_t>(src) & 15) == 0)) {
+          v = __ldg(reinterpret_cast<const float4*>(src));
+        } else {
+          if (x < xe) { const float2 a = __ldg(src); v.x = a.x; v.y = a.y; }
+          if (x + 1 < xe) { const float2 b = __ldg(src + 1); v.z = b.x; v.w = b.y; }
+        }
       }
-      put(Bhi, Blo, 2 * m, 2 * j, cs);
-      put(Bhi, Blo, 2 * m, 2 * j + 1, sn);
-      put(Bhi, Blo, 2 * m + 1, 2 * j, -sn);
-      put(Bhi, Blo, 2 * m + 1, 2 * j + 1, cs);
+      va[i] = v;
+    }
+  };
+  if (nchunks > 0) load_a(0);
+  if (tid == 0 && nchunks > 0) {  // B of chunk 0
+    const uint32_t bb = ptx::smem_addr(smem + 2 * a_bytes);
+    ptx::mbar_arrive_expect_tx(ptx::smem_addr(bar + 2), 2 * b_bytes);
+    ptx::bulk_g2s(bb, tiles + (size_t)(xb / kChunk) * 2 * (b_bytes / 16), 2 * b_bytes, ptx::smem_addr(bar + 2));
+  }
+
+  bool ok = true;
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int s = c & 1;
+    unsigned char* st = smem + s * stage_bytes;
+    // write this chunk's A (in registers) into stage s
+#pragma unroll
+    for (int i = 0; i < kAPer; ++i) {
+      const int u = warp + 4 * i;
+      const int rg = u / (kKt / 16), kc = (u % (kKt / 16)) * 4 + (lane >> 3);
+      float4 hi, lo;
+      split4(va[i], hi, lo);
+      const uint32_t o = core_row(rg * 8 + (lane & 7), kc);
+      *reinterpret_cast<float4*>(st + o) = hi;
+      *reinterpret_cast<float4*>(st + a_bytes + o) = lo;
     }
     ptx::fence_proxy_async_smem();
     __syncthreads();
     if (tid == 0) {
-      ptx::tc_fence_after();
-      const uint32_t ah = ptx::smem_addr(Ahi), al = ptx::smem_addr(Alo);
-      const uint32_t bh = ptx::smem_addr(Bhi), bl = ptx::smem_addr(Blo);
-      const uint32_t sbo_a = kKt * 32, sbo_b = kKt * 32;
-#pragma unroll 1
-      for (int s = 0; s < kKt / 8; ++s) {
-        const uint32_t off = s * 256;  // two core matrices along K per instruction
-        const uint64_t dah = ptx::smem_desc_noswizzle(ah + off, 128, sbo_a);
-        const uint64_t dal = ptx::smem_desc_noswizzle(al + off, 128, sbo_a);
-        const uint64_t dbh = ptx::smem_desc_noswizzle(bh + off, 128, sbo_b);
-        const uint64_t dbl = ptx::smem_desc_noswizzle(bl + off, 128, sbo_b);
-        ptx::mma_tf32(tmem, dah, dbh, idesc, issued ? 1u : 0u);
-        issued = true;
-        ptx::mma_tf32(tmem, dah, dbl, idesc, 1u);
-        ptx::mma_tf32(tmem, dal, dbh, idesc, 1u);
+      const bool bin = ptx::mbar_wait_bounded(ptx::smem_addr(bar + 2 + s), (c >> 1) & 1, timeout_ns);
+      if (bin) {
+        ptx::tc_fence_after();
+        const uint32_t ah = ptx::smem_addr(st), al = ah + a_bytes, bh = al + a_bytes, bl = bh + b_bytes;
+        const uint32_t sbo = (kKt / 4) * 128;
+#pragma unroll
+        for (int k = 0; k < kKt / 8; ++k) {
+          const uint32_t off = k * 256;  // two core matrices along K per instruction
+          const uint64_t dah = ptx::smem_desc_noswizzle(ah + off, 128, sbo);
+          const uint64_t dal = ptx::smem_desc_noswizzle(al + off, 128, sbo);
+          const uint64_t dbh = ptx::smem_desc_noswizzle(bh + off, 128, sbo);
+          const uint64_t dbl = ptx::smem_desc_noswizzle(bl + off, 128, sbo);
+          ptx::mma_tf32(tmem, dah, dbh, idesc, (c > 0 || k > 0) ? 1u : 0u);
+          ptx::mma_tf32(tmem, dah, dbl, idesc, 1u);
+          ptx::mma_tf32(tmem, dal, dbh, idesc, 1u);
+        }
+        ptx::mma_commit(ptx::smem_addr(bar + s));
+      } else {
+        atomicOr(status, kStatusFullWait);
       }
-      ptx::mma_commit(bar_a);
     }
-    issued = true;
-    // the staged operands are overwritten only after the tensor cores read them
-    const bool done = ptx::mbar_wait_bounded(bar_a, phase, timeout_ns);
-    phase ^= 1;
+    // next chunk: its loads go out before this thread waits for stage s ^ 1
+    if (c + 1 < nchunks) load_a(c + 1);
+    if (c >= 1) {  // the tensor cores have read chunk c - 1 from stage s ^ 1
+      const bool done = ptx::mbar_wait_bounded(ptx::smem_addr(bar + (s ^ 1)), ((c - 1) >> 1) & 1, timeout_ns);
+      if (!__syncthreads_and(done ? 1 : 0)) {
+        ok = false;
+        break;
+      }
+      ptx::tc_fence_after();
+    }
+    if (tid == 0 && c + 1 < nchunks) {  // B of chunk c + 1 into stage s ^ 1
+      const uint32_t bb = ptx::smem_addr(smem + (s ^ 1) * stage_bytes + 2 * a_bytes);
+      ptx::mbar_arrive_expect_tx(ptx::smem_addr(bar + 2 + (s ^ 1)), 2 * b_bytes);
+      ptx::bulk_g2s(bb, tiles + (size_t)(xb / kChunk + c + 1) * 2 * (b_bytes / 16), 2 * b_bytes,
+                    ptx::smem_addr(bar + 2 + (s ^ 1)));
+    }
+  }
+  if (ok && nchunks > 0) {  // the last commit covers every MMA issued before it
+    const int c = nchunks - 1;
+    const bool done = ptx::mbar_wait_bounded(ptx::smem_addr(bar + (c & 1)), (c >> 1) & 1, timeout_ns);
     ok = __syncthreads_and(done ? 1 : 0) != 0;
     ptx::tc_fence_after();
   }
-
   if (!ok) {
-    if (tid == 0) atomicOr(status, kStatusFullWait);
-  } else if (issued) {
-    // epilogue: warp w owns TMEM lanes (rows) 32w..32w+31
+    // a wait ran out: record it and give the outstanding copies and MMAs one
+    // more bounded wait so that nothing writes this CTA's buffers after it exits
+    if (tid == 0) {
+      atomicOr(status, kStatusFullWait);
+      for (int c = max(0, nchunks - 2); c < nchunks; ++c) {
+        if (!ptx::mbar_wait_bounded(ptx::smem_addr(bar + 2 + (c & 1)), (c >> 1) & 1, timeout_ns))
+          atomicOr(status, kStatusDrain);
+        if (!ptx::mbar_wait_bounded(ptx::smem_addr(bar + (c & 1)), (c >> 1) & 1, timeout_ns))
+          atomicOr(status, kStatusDrain);
+      }
+    }
+  } else {
+    // epilogue: warp w owns TMEM lanes (rows) 32w..32w+31; partial[split][col][row]
     const int row = row0 + warp * 32 + lane;
     const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16);
-    const double scale = ldexp(1.0, (P.ra ? P.ca * P.ra->exp : 0) + (P.rb ? P.cb * P.rb->exp : 0));
+    float* dst = partial + (size_t)blockIdx.y * P.npad * P.rows;
     for (int c0 = 0; c0 < P.npad; c0 += 16) {
       float v[16];
-      ptx::tmem_ld16(taddr + c0, v);
-      if (row < P.rows) {
-        const int chan = row / P.Nt, t = row % P.Nt;
+      if (nchunks > 0) {
+        ptx::tmem_ld16(taddr + c0, v);
+      } else {
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const int m = (c0 + i) / 2;
-          if (m < P.nmom) {
-            const long long o = ((long long)chan * P.nmom + m) * P.Nt + t;
-            atomicAdd(out + 2 * o, (double)v[i] * scale);
-            atomicAdd(out + 2 * o + 1, (double)v[i + 1] * scale);
-          }
-        }
+        for (int i = 0; i < 16; ++i) v[i] = 0.f;
+      }
+      if (row < P.rows) {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) dst[(size_t)(c0 + i) * P.rows + row] = v[i];
       }
     }
   }
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
-  if (warp == 0) ptx::tmem_dealloc(tmem, kTmemCols);
+  if (warp == 0) ptx::tmem_dealloc(tmem, tcols);
+}
+
+// s + e = a + b exactly (Knuth's TwoSum).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  const float x = __fadd_rn(a, b);
+  const float bv = __fsub_rn(x, a);
+  const float av = __fsub_rn(x, bv);
+  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
+  s = x;
+}
+
+// out[(chan * nmom + m) * Nt + t] = 2^e * sum over the site splits of the
+// partial sums: one warp per output, each lane a strided share of the
+// splits, all in two-float arithmetic (hi + lo), FP64 once at the end.
+__global__ void __launch_bounds__(256) momproj_fold_kernel(const float* __restrict__ partial, int nsplit, int rows,
+                                                           int npad, int nmom, int Nt, double* __restrict__ out,
+                                                           const ScaleRecord* ra, int ca, const ScaleRecord* rb,
+                                                           int cb) {
+  const long long total = (long long)rows * nmom;
+  const long long w = blockIdx.x * 8LL + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (w >= total) return;
+  const int row = (int)(w % rows), m = (int)(w / rows);
+  float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
+  for (int sp = lane; sp < nsplit; sp += 32) {
+    const float* p = partial + (size_t)sp * npad * rows;
+    float e;
+    two_sum(hr, p[(size_t)(2 * m) * rows + row], hr, e);
+    lr += e;
+    two_sum(hi, p[(size_t)(2 * m + 1) * rows + row], hi, e);
+    li += e;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float a = __shfl_xor_sync(0xffffffffu, hr, o), b = __shfl_xor_sync(0xffffffffu, lr, o);
+    const float c = __shfl_xor_sync(0xffffffffu, hi, o), d = __shfl_xor_sync(0xffffffffu, li, o);
+    float e;
+    two_sum(hr, a, hr, e);
+    lr += b + e;
+    two_sum(hi, c, hi, e);
+    li += d + e;
+  }
+  if (lane == 0) {
+    const int ex = (ra ? ca * ra->exp : 0) + (rb ? cb * rb->exp : 0);
+    const int chan = row / Nt, t = row % Nt;
+    const long long o = ((long long)chan * nmom + m) * Nt + t;
+    out[2 * o] = ldexp((double)hr + (double)lr, ex);
+    out[2 * o + 1] = ldexp((double)hi + (double)li, ex);
+  }
 }
 
 }  // namespace
@@ -197,15 +338,13 @@ int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* 
   if (n_chan < 1) return fail(QDPG_ERR_ARG, "momentum_project: n_chan %d < 1", n_chan);
   if (n_mom < 1 || n_mom > kMaxMomP) return fail(QDPG_ERR_ARG, "momentum_project: n_mom %d outside 1..%d", n_mom, kMaxMomP);
   if (reinterpret_cast<uintptr_t>(sites_dev) % 8) return fail(QDPG_ERR_ARG, "momentum_project: sites not 8-byte aligned");
+  for (int k = 0; k < 3; ++k)
+    if (g.sL[k] > kMaxL) return fail(QDPG_ERR_UNSUPPORTED, "momentum_project: spatial extent above %d", kMaxL);
   const long long rows = (long long)n_chan * g.Nt;
   if (rows > (1LL << 30)) return fail(QDPG_ERR_ARG, "momentum_project: too many rows");
   unsigned int* status = device_status_word();
   if (!status) return fail(QDPG_ERR_CUDA, "momentum_project: no status word");
   ProjArgs P{};
-  P.ra = ra;
-  P.rb = rb;
-  P.ca = ca;
-  P.cb = cb;
   P.rows = (int)rows;
   P.Nt = g.Nt;
   P.V3 = g.V3;
@@ -218,25 +357,57 @@ int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* 
   for (int m = 0; m < n_mom; ++m)
     for (int k = 0; k < 3; ++k) P.k[m][k] = moms[3 * m + k];
   const int row_tiles = (int)((rows + kM - 1) / kM);
-  // split the sites so that about two waves of CTAs run; at least 32 sites
-  // each, and at most kMaxAccSites: the tensor-core accumulator is FP32, so
-  // its depth bounds the rounding error; longer sums go through the FP64
-  // atomics across CTAs
-  int nsplit = std::max(1, std::min((g.V3 + kChunk - 1) / kChunk, (2 * 152 + row_tiles - 1) / row_tiles));
-  nsplit = std::max(nsplit, (g.V3 + kMaxAccSites - 1) / kMaxAccSites);
-  P.sites_per_cta = ((g.V3 + nsplit - 1) / nsplit + kChunk - 1) / kChunk * kChunk;
+  // split the sites so that about one wave of CTAs (two per SM) runs, each
+  // with at most kMaxCtaSites sites: the tensor-core accumulator is FP32, and
+  // its depth bounds the rounding error; longer sums add up in the FP64 fold
+  const int nchunk_all = (g.V3 + kChunk - 1) / kChunk;
+  int nsplit = std::max(1, std::min(nchunk_all, (2 * 152 + row_tiles - 1) / row_tiles));
+  nsplit = std::max(nsplit, (g.V3 + kMaxCtaSites - 1) / kMaxCtaSites);
+  P.sites_per_cta = (nchunk_all + nsplit - 1) / nsplit * kChunk;
   nsplit = (g.V3 + P.sites_per_cta - 1) / P.sites_per_cta;
-  const size_t smem = (size_t)2 * kM * kKt * 4 + (size_t)2 * P.npad * kKt * 4 + 16;
+  const size_t stage_bytes = (size_t)2 * kM * kKt * 4 + (size_t)2 * P.npad * kKt * 4;
+  const size_t smem = 2 * stage_bytes + 4 * sizeof(uint64_t) + 16;
+  const int nchunk_pad = (g.V3 + kChunk - 1) / kChunk;
+  const size_t tile_bytes = (size_t)nchunk_pad * 2 * P.npad * kKt * 4;
 
-  cudaError_t e = cudaMemsetAsync(out_dev, 0, sizeof(double) * 2 * (size_t)rows * n_mom, s);
-  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "momentum_project: memset: %s", cudaGetErrorString(e));
-  e = cudaFuncSetAttribute(momproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "momentum_project: smem attribute: %s", cudaGetErrorString(e));
-  dim3 grid(row_tiles, nsplit);
-  ProfScope prof("momentum_project", s);
-  momproj_kernel<<<grid, 128, smem, s>>>(static_cast<const float2*>(sites_dev), P, out_dev, status,
-                                         wait_timeout_ns());
-  return check_launch("momentum_project");
+  void* partial = nullptr;
+  void* tiles = nullptr;
+  int rc = dev_alloc(&partial, sizeof(float) * (size_t)nsplit * P.npad * rows, s, "momentum_project partial sums");
+  if (rc == QDPG_OK) rc = dev_alloc(&tiles, tile_bytes, s, "momentum_project phase tiles");
+  if (rc != QDPG_OK) {
+    dev_free(partial, s);
+    return rc;
+  }
+  cudaError_t e = cudaFuncSetAttribute(momproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    dev_free(partial, s);
+    dev_free(tiles, s);
+    return fail(QDPG_ERR_CUDA, "momentum_project: smem attribute: %s", cudaGetErrorString(e));
+  }
+  {
+    ProfScope prof("momentum_project", s);
+    const long long ntask = (long long)nchunk_pad * P.npad * (kKt / 4);
+    phase_tile_kernel<<<(int)std::min<long long>((ntask + 255) / 256, 152LL * 8), 256, 0, s>>>(
+        P, static_cast<float4*>(tiles));
+    rc = check_launch("momentum_project phases");
+    if (rc == QDPG_OK) {
+      momproj_kernel<<<dim3(row_tiles, nsplit), 128, smem, s>>>(static_cast<const float2*>(sites_dev), P,
+                                                                  static_cast<const float4*>(tiles),
+                                                                  static_cast<float*>(partial), status,
+                                                                  wait_timeout_ns());
+      rc = check_launch("momentum_project");
+    }
+    if (rc == QDPG_OK) {
+      const long long nout = rows * n_mom;
+      momproj_fold_kernel<<<(int)((nout + 7) / 8), 256, 0, s>>>(static_cast<const float*>(partial), nsplit,
+                                                                  (int)rows, P.npad, n_mom, g.Nt, out_dev, ra, ca,
+                                                                  rb, cb);
+      rc = check_launch("momentum_project fold");
+    }
+  }
+  dev_free(tiles, s);
+  dev_free(partial, s);
+  return rc;
 }
 
 }  // namespace qdpg

@@ -108,6 +108,7 @@ int debug_f16_warps();       // consumer warps of the float16 smearing kernel, 0
 // `what` on failure, including failures forced by QDPG_DEBUG_FAIL_ALLOCS.
 int dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
 long long debug_stage_bytes();  // chunk bound of the host-buffer import/export, 0 = default
+int debug_meson_unstaged();     // 1: meson contractions read S2 from global memory (no staging)
 void dev_free(void* p, cudaStream_t s);
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage

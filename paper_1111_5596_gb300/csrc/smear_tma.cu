@@ -6,6 +6,7 @@
 #include <tuple>
 
 #include "smear_tma.cuh"
+#include "tmap.h"
 
 namespace qdpg {
 
@@ -121,6 +122,23 @@ EncodeTiledFn encode_tiled() {
   });
   return fn;
 }
+
+}  // namespace
+
+bool encode_map_2d(CUtensorMap* m, const void* base, int esize, uint64_t dim0, uint64_t dim1, uint64_t row_bytes,
+                   uint32_t box0, uint32_t box1) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn || (esize != 4 && esize != 8)) return false;
+  const cuuint64_t dims[2] = {dim0, dim1};
+  const cuuint64_t strides[1] = {row_bytes};
+  const cuuint32_t box[2] = {box0, box1};
+  const cuuint32_t estr[2] = {1, 1};
+  return fn(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base),
+            dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
 
 // The input propagator of one job as the 4-D tensor of the whole-plane
 // tensor-map copies: (x; row = y + Ly*z; the 12 colour vectors of a spin

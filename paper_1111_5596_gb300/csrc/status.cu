@@ -24,6 +24,7 @@ int g_f16_warps = 0;  // 0: the library's default (16)
 int g_tensor_copy_off = 0;  // 1: the pipelined hop stages with bulk copies only
 int g_fail_allocs = 0;      // the next this many device allocations fail (test hook)
 long long g_stage_bytes = 0;  // host import/export chunk bound, 0 = default
+int g_meson_unstaged = 0;     // 1: the meson contraction without the shared-memory staging
 std::atomic<uint64_t> g_allocs{0};
 
 }  // namespace
@@ -49,6 +50,41 @@ int debug_tile_grid() { return g_tile_grid; }
 int debug_f16_warps() { return g_f16_warps; }
 int debug_tensor_copy_off() { return g_tensor_copy_off; }
 long long debug_stage_bytes() { return g_stage_bytes; }
+int debug_meson_unstaged() { return g_meson_unstaged; }
+
+// The library's memory pool on the current device, created on first use:
+// its own stream-ordered pool (not the device's default one), which keeps up
+// to kPoolKeepBytes of freed memory mapped between calls instead of handing
+// it back at every synchronisation, so a repeated call does not map its
+// temporaries anew.
+constexpr uint64_t kPoolKeepBytes = uint64_t(4) << 30;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaError_t lib_pool(cudaMemPool_t* out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    e = cudaMemPoolCreate(&pool, &props);
+    if (e != cudaSuccess) return e;
+    uint64_t keep = kPoolKeepBytes;
+    e = cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      cudaMemPoolDestroy(pool);
+      return e;
+    }
+    g_pool[dev] = pool;
+  }
+  *out = g_pool[dev];
+  return cudaSuccess;
+}
 
 int dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
   *p = nullptr;
@@ -59,7 +95,10 @@ int dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what) {
       return fail(QDPG_ERR_NOMEM, "%s: allocation of %zu bytes refused (test hook)", what, bytes);
     }
   }
-  const cudaError_t e = cudaMallocAsync(p, bytes, s);
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = lib_pool(&pool);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "%s: memory pool: %s", what, cudaGetErrorString(e));
+  e = cudaMallocFromPoolAsync(p, bytes, pool, s);
   if (e != cudaSuccess) {
     *p = nullptr;
     cudaGetLastError();  // the failed allocation leaves no sticky error
@@ -80,6 +119,15 @@ using namespace qdpg;
 extern "C" {
 
 uint64_t qdpg_device_alloc_count(void) { return g_allocs.load(std::memory_order_relaxed); }
+
+int qdpg_device_pool_used(uint64_t* bytes) {
+  if (!bytes) return fail(QDPG_ERR_ARG, "device_pool_used: null argument");
+  cudaMemPool_t pool = nullptr;
+  cudaError_t e = lib_pool(&pool);
+  if (e == cudaSuccess) e = cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, bytes);
+  if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "device_pool_used: %s", cudaGetErrorString(e));
+  return ok();
+}
 
 int qdpg_device_status(void* stream) {
   unsigned int* w = device_status_word();
@@ -132,6 +180,10 @@ int qdpg_debug_set(int what, long long value) {
     case QDPG_DEBUG_STAGE_BYTES:
       if (value < 0 || value > (1LL << 40)) return fail(QDPG_ERR_ARG, "debug_set: staging bytes outside 0..2^40");
       g_stage_bytes = value;
+      return ok();
+    case QDPG_DEBUG_MESON_UNSTAGED:
+      if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: meson staging setting outside 0..1");
+      g_meson_unstaged = (int)value;
       return ok();
     case QDPG_DEBUG_FAIL_ALLOCS:
       if (value < 0 || value > 1000000) return fail(QDPG_ERR_ARG, "debug_set: failing allocations outside 0..1e6");

@@ -7,8 +7,8 @@ ping-pong buffer is the library's 32 MiB static device array.  The test calls
 it through the C ABI twice in a row -- the second call finds the first call's
 data still in the shared array -- and compares each result with
 qdpg_gauss_smear given a caller-owned scratch field.  It also checks that the
-calls allocate nothing: the library's own allocation counter, torch's
-caching allocator and the CUDA memory pool of the device stay unchanged.
+calls allocate nothing: the library's own allocation counter, the bytes in
+use in its memory pool and torch's caching allocator stay unchanged.
 FP32 and BF16 storage are covered, and a smearing long enough (kappa = 0.3,
 N = 60) that the power-of-two rescaling runs through the static scratch.
 """
@@ -36,24 +36,11 @@ def _field(q, lat, kind, canon, prec=None):
     return f.import_(torch.from_numpy(canon.astype(np.complex64)).to("cuda:0"))
 
 
-def _pool_used():
-    """Bytes in use in the device's default CUDA memory pool (stream-ordered allocations)."""
-    from cuda.bindings import runtime as rt
-
-    err, pool = rt.cudaDeviceGetDefaultMemPool(0)
-    assert err == rt.cudaError_t.cudaSuccess
-    err, used = rt.cudaMemPoolGetAttribute(pool, rt.cudaMemPoolAttr.cudaMemPoolAttrUsedMemCurrent)
-    assert err == rt.cudaError_t.cudaSuccess
-    return int(used)
-
-
 def _memory_state(q):
+    """The library's allocation counter and its pool's bytes in use, and
+    torch's caching allocator (all unchanged by a call that allocates nothing)."""
     torch.cuda.synchronize()
-    try:
-        pool = _pool_used()
-    except ImportError:                          # cuda-bindings absent: the other two figures stand
-        pool = None
-    return q.device_alloc_count(), torch.cuda.memory_allocated(), pool
+    return q.device_alloc_count(), q.device_pool_used(), torch.cuda.memory_allocated()
 
 
 @pytest.mark.parametrize("kind,prec,dims,n_iter,kappa", [
