@@ -69,6 +69,9 @@ def parse_args():
                     help="skip the 64-job batched comparison (FP32 one job at a time vs batched FP32/BF16)")
     ap.add_argument("--batch-steps", type=int, default=5)
     ap.add_argument("--no-24x48", action="store_true", help="skip the 24^3x48 smearing-hop roofline component")
+    ap.add_argument("--partition", choices=["replica", "tslab"], default="replica",
+                    help="replica: every rank runs its own lattice (weak scaling); tslab: the ranks split one "
+                         "lattice into timeslice slabs and gather the correlators (strong scaling)")
     ap.add_argument("--no-scale", action="store_true",
                     help="skip the 48^3x96 scale run (8 propagators, 64 meson pairs + nucleon at 33 momenta)")
     return ap.parse_args()
@@ -670,11 +673,25 @@ def gpu_arm(args):
     q.load()
 
     base = workload()
-    w = configs.Workload(base.name, base.dims, base.links, base.kappa, base.n_smear, base.prop, eps=base.eps,
-                         seed=base.seed + 1000 * rank)          # independent problem per rank
-    lat = q.Lattice(w.dims, w.j_decay)
-    U_h = torch.from_numpy(fields.gauge_field(w.dims, w.seed, kind=w.links, eps=w.eps).astype(np.complex64))
-    P_h = torch.from_numpy(fields.propagator(w.dims, w.seed).astype(np.complex64))
+    tslab_mode = args.partition == "tslab" and world > 1
+    if tslab_mode:
+        # one lattice split by timeslices: this rank's slab [t0, t0 + nt), same seeds on every rank
+        from paper_1111_5596_gb300 import tslab
+
+        w = base
+        t0, nt = tslab.slab(w.Nt, world, rank)
+        lat = q.Lattice(tslab.slab_dims(w.dims, w.j_decay, nt), w.j_decay)
+        sub = lat.dims
+        U_h = torch.from_numpy(fields.gauge_field(w.dims, w.seed, kind=w.links, eps=w.eps, x3_range=(t0, t0 + nt))
+                               .reshape((4,) + tuple(reversed(sub)) + (3, 3)).astype(np.complex64))
+        P_h = torch.from_numpy(fields.propagator(w.dims, w.seed, x3_range=(t0, t0 + nt)).astype(np.complex64))
+    else:
+        t0, nt = 0, base.Nt
+        w = configs.Workload(base.name, base.dims, base.links, base.kappa, base.n_smear, base.prop, eps=base.eps,
+                             seed=base.seed + 1000 * rank)          # independent problem per rank
+        lat = q.Lattice(w.dims, w.j_decay)
+        U_h = torch.from_numpy(fields.gauge_field(w.dims, w.seed, kind=w.links, eps=w.eps).astype(np.complex64))
+        P_h = torch.from_numpy(fields.propagator(w.dims, w.seed).astype(np.complex64))
     U_h, P_h = U_h.pin_memory(), P_h.pin_memory()
     U_dev, P_dev = U_h.to(dev), P_h.to(dev)
 
@@ -682,18 +699,29 @@ def gpu_arm(args):
     src = q.Field(lat, q.PROPAGATOR, q.F32, device=dev)
     snk = q.Field(lat, q.PROPAGATOR, q.F32, device=dev)
     scratch = q.Field(lat, q.PROPAGATOR, q.F32, device=dev)
-    C = torch.empty((16, 1, w.Nt), dtype=torch.complex128, device=dev)
-    C_h = torch.empty_like(C, device="cpu").pin_memory()
+    C = torch.empty((16, 1, lat.Nt), dtype=torch.complex128, device=dev)
+    C_h = torch.empty((16, 1, w.Nt), dtype=torch.complex128).pin_memory()
+    if tslab_mode and t0 != 0:
+        src.storage.zero_()   # the point source (origin) lies on rank 0's slab; this slab's source is zero
 
     # launch shapes of the smearing kernel, picked by measurement before timing
     tuned = (None, None) if args.no_tune else q.tune_smear(U, snk.import_(P_dev), scratch, w.j_decay, reps=3)
 
+    def source():
+        if t0 == 0:
+            q.point_source(src)
+
+    def correlators():
+        # the slabs' correlators gathered over the ranks (tslab); the whole lattice's otherwise
+        return tslab.gather_timeslices(C, w.Nt, world, rank) if tslab_mode else C
+
     def step_device():
         snk.import_(P_dev)
-        q.point_source(src)
+        source()
         q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
         q.gauss_smear(U, snk, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
         q.meson_2pt(snk, snk, q.SIXTEEN_MESONS, out=C)
+        return correlators()
 
     def barrier():
         if world > 1:
@@ -754,10 +782,12 @@ def gpu_arm(args):
 
     b = step_bytes(w)
     peaks = measured_peaks()
-    value = whole_job_rate(world, b["total"], ms * 1e-3) / 1e9
+    # tslab: the ranks share one lattice (its bytes once); replicas: each rank's lattice counts
+    value = (b["total"] / (ms * 1e-3) if tslab_mode else whole_job_rate(world, b["total"], ms * 1e-3)) / 1e9
 
     hop_ms, hop_n = kern["smear_hop"]
     hop_avg_s = hop_ms / hop_n * 1e-3
+    b["hop_per_launch"] = lat.V * (144 * 8 * 2 + 3 * 9 * 8)   # this rank's lattice (a slab under tslab)
     achieved = b["hop_per_launch"] / hop_avg_s / 1e9
     mes_ms, mes_n = kern["meson_2pt"]
     smear_s = hop_ms * 1e-3 / args.steps
@@ -768,11 +798,12 @@ def gpu_arm(args):
                 "back_to_back_us": hop_b2b_s * 1e6,
                 "frac_back_to_back": b["hop_per_launch"] / hop_b2b_s / 1e9 / peaks["hbm_gbs"],
                 "launches": hop_n, "tuned_tile_sites": tuned[0], "tuned_grid_mode": tuned[1]}
+    b_rank = step_bytes(w, n_timeslices=lat.Nt)   # this rank's share (its slab under tslab)
     components = {
-        "smear_gbs_kernel": (b["smear_src"] + b["smear_snk"]) / smear_s / 1e9,
+        "smear_gbs_kernel": (b_rank["smear_src"] + b_rank["smear_snk"]) / smear_s / 1e9,
         "smear_hbm_frac": achieved / peaks["hbm_gbs"],
-        "contraction_sites_per_s": w.V / (mes_ms / mes_n * 1e-3),
-        "contraction_gbs": b["mesons"] / (mes_ms / mes_n * 1e-3) / 1e9,
+        "contraction_sites_per_s": lat.V / (mes_ms / mes_n * 1e-3),
+        "contraction_gbs": b_rank["mesons"] / (mes_ms / mes_n * 1e-3) / 1e9,
         "kernel_ms_per_step": {k: v[0] / args.steps for k, v in kern.items()},
     }
 
@@ -790,12 +821,12 @@ def gpu_arm(args):
             copy_stream.wait_stream(stream)
             snk.import_host(P_h, stream=copy_stream)
             P_done.record(copy_stream)
-            q.point_source(src)
+            source()
             q.gauss_smear(U, src, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
             stream.wait_event(P_done)
             q.gauss_smear(U, snk, w.kappa, w.n_smear, w.j_decay, scratch=scratch)
             q.meson_2pt(snk, snk, q.SIXTEEN_MESONS, out=C)
-            C_h.copy_(C, non_blocking=True)
+            C_h.copy_(correlators(), non_blocking=True)
             stream.synchronize()
             return C_h
 
@@ -809,7 +840,8 @@ def gpu_arm(args):
         barrier()
         e2e_s = max_over_ranks((time.perf_counter() - t0) / args.steps, world, dev)
         h2d = U_h.numel() * U_h.element_size() + P_h.numel() * P_h.element_size()
-        e2e = {"value": whole_job_rate(world, b["total"], e2e_s) / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
+        e2e_rate = b["total"] / e2e_s if tslab_mode else whole_job_rate(world, b["total"], e2e_s)
+        e2e = {"value": e2e_rate / 1e9, "unit": "GB/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": C_h.numel() * C_h.element_size(), "ms_per_step": e2e_s * 1e3,
                "path": "qdpg_field_import_host (page-locked canonical complex64) for links and propagator, "
                        "correlators read back every step"}
@@ -833,11 +865,14 @@ def gpu_arm(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "strong" if tslab_mode else "weak",
             "vs_baseline": None, "dtype": "f32",
             "data": "synthetic: seeded near-unit SU(3) links (eps=0.3) and Gaussian propagator with "
                     "exp(-0.5|x|) envelope, complex64",
-            "config": config_block(w), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "config": dict(config_block(w), **({"parallelism": f"tslab{world}: one lattice in timeslice slabs, "
+                                                                  "correlators gathered (NCCL all_gather) every step"}
+                                                 if tslab_mode else {})), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "components": components,
         }
         print(json.dumps(line), flush=True)
