@@ -166,9 +166,12 @@ int qdpg_device_status(void* stream);
  *                              (the calls return QDPG_ERR_NOMEM); 0 = none;
  *  QDPG_DEBUG_STAGE_BYTES      largest chunk (bytes of canonical data, at least one
  *                              timeslice) of the host-buffer import/export; 0 = 256 MiB;
- *  QDPG_DEBUG_MESON_UNSTAGED   1: F32/BF16 meson contractions read S2 from global memory
- *                              for every mask pair instead of staging it in shared
- *                              memory (the two give the same values); 0 = staged;
+ *  QDPG_DEBUG_MESON_FORM       kernel of the F32/BF16 meson contractions: 0 (default) the
+ *                              best that applies (the orbit kernel where every channel's
+ *                              two masks are equal, as for the sixteen mesons), 1 the
+ *                              kernel that stages S2 in shared memory, 2 the kernel that
+ *                              reads both propagators from global memory (the forms agree
+ *                              to FP32 rounding);
  * and launch-shape settings of the pipelined smearing kernel:
  *  QDPG_TUNE_TILE_CONSUMERS    most sites (threads) per tile, 32..288, 0 = default;
  *  QDPG_TUNE_STAGES            pipeline depth 2..16, 0 = as many as fit (0);
@@ -189,7 +192,7 @@ enum {
   QDPG_TUNE_TENSOR_COPY = 9,
   QDPG_DEBUG_FAIL_ALLOCS = 11,
   QDPG_DEBUG_STAGE_BYTES = 12,
-  QDPG_DEBUG_MESON_UNSTAGED = 13
+  QDPG_DEBUG_MESON_FORM = 13
 };
 int qdpg_debug_set(int what, long long value);
 
@@ -353,6 +356,26 @@ int qdpg_gauss_smear_noalloc(qdpg_field_t U, qdpg_field_t psi, double kappa, int
 int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src,
                    int n_chan, const int* moms, int n_mom, const int origin[4], double* out_dev,
                    void* stream);
+
+/* All ordered pairs of a set of propagators in one pass (Sec. 5: the hadron
+ * spectrum of many smeared sources and sinks at once):
+ *   out[a][b][j][k][t] = the qdpg_meson_2pt value of S1 = props[a],
+ *                        S2 = props[b], channel j, momentum k, timeslice t
+ * for a, b = 0..n_props-1.  Every site of every propagator is read once for
+ * all n_props^2 pairs (an F32 48^3x96 propagator is 12.2 GB: 8 of them read
+ * once instead of 64 pairwise reads of two each).  The per-site traces of all
+ * pairs and channels go, a batch of timeslices at a time (at most 4 GiB of
+ * site values), to a library buffer and are projected on the tensor cores
+ * (qdpg_momentum_project), each pair's sums multiplied by 2^(exp_a + exp_b).
+ * props: 1..8 PROPAGATOR fields, all F32 or all BF16, same lattice.
+ * Channels: 1..16, each with Gamma_snk and Gamma_src that permute spin alike
+ * (true for Gamma_snk = Gamma_src, as for the sixteen mesons; others return
+ * QDPG_ERR_UNSUPPORTED).  moms, n_mom, origin as in qdpg_meson_2pt.
+ * out_dev: device buffer of n_props^2*n_chan*n_mom*Nt complex doubles,
+ * overwritten.  QDPG_ERR_NOMEM if the library's buffers cannot be allocated. */
+int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, const int* gamma_snk, const int* gamma_src,
+                         int n_chan, const int* moms, int n_mom, const int origin[4], double* out_dev,
+                         void* stream);
 
 /* ---- baryon two-point functions (Sec. 5: HAD, baryonic) ----------------- */
 

@@ -74,6 +74,7 @@ def load() -> ctypes.CDLL:
         "qdpg_gauss_smear": (i, [vp, vp, d, i, i, vp, vp]),
         "qdpg_gauss_smear_noalloc": (i, [vp, vp, d, i, i, vp]),
         "qdpg_meson_2pt": (i, [vp, vp, ip, ip, i, ip, i, ip, vp, vp]),
+        "qdpg_meson_2pt_multi": (i, [ctypes.POINTER(vp), i, ip, ip, i, ip, i, ip, vp, vp]),
         "qdpg_baryon_2pt": (i, [vp, vp, i, i, ip, i, ip, vp, vp]),
         "qdpg_meson_sites": (i, [vp, vp, ip, ip, i, vp, vp]),
         "qdpg_baryon_sites": (i, [vp, vp, i, i, vp, vp]),
@@ -124,7 +125,7 @@ def launch_count() -> int:
 
 
 DEBUG_WAIT_TIMEOUT_NS, DEBUG_DROP_STAGE, DEBUG_FORCE_SIMPLE_HOP = 1, 2, 3
-DEBUG_FAIL_ALLOCS, DEBUG_STAGE_BYTES, DEBUG_MESON_UNSTAGED = 11, 12, 13
+DEBUG_FAIL_ALLOCS, DEBUG_STAGE_BYTES, DEBUG_MESON_FORM = 11, 12, 13
 TUNE_TILE_CONSUMERS, TUNE_STAGES, TUNE_GRID, TUNE_TENSOR_COPY = 4, 5, 7, 9
 
 
@@ -363,6 +364,27 @@ def meson_2pt(S1: Field, S2: Field, channels, moms=((0, 0, 0),), origin=None, ou
                                len(channels), _ints(flat), len(moms),
                                _ints(origin) if origin is not None else None,
                                ctypes.c_void_p(out.data_ptr()), _stream(stream)))
+    return out
+
+
+def meson_2pt_multi(props, channels, moms=((0, 0, 0),), origin=None, out=None, stream=None):
+    """Meson correlators of every ordered pair of the propagators in one pass,
+    complex128 CUDA tensor (n, n, n_chan, n_mom, Nt): out[a, b] is
+    meson_2pt(props[a], props[b], ...)."""
+    import torch
+
+    props = list(props)
+    channels = list(channels)
+    moms = [tuple(m) for m in moms]
+    n, nt = len(props), props[0].lattice.Nt
+    if out is None:
+        out = torch.empty((n, n, len(channels), len(moms), nt), dtype=torch.complex128, device=props[0].storage.device)
+    handles = (ctypes.c_void_p * n)(*[p._h.value for p in props])
+    flat = [c for m in moms for c in m]
+    _check(_lib.qdpg_meson_2pt_multi(handles, n, _ints([c[0] for c in channels]), _ints([c[1] for c in channels]),
+                                     len(channels), _ints(flat), len(moms),
+                                     _ints(origin) if origin is not None else None,
+                                     ctypes.c_void_p(out.data_ptr()), _stream(stream)))
     return out
 
 

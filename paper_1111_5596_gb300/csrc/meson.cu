@@ -23,6 +23,7 @@
 // atomic per block and value.
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <cstring>
 #include <type_traits>
 #include <vector>
@@ -51,6 +52,7 @@ struct MesonPass {
   int out_row[kMaxPassCh];       // channel index in the output
   float2 w[kMaxPassCh][16];      // weight of Q_q[alpha*4 + beta]
   int jlo[4], jhi[4];            // channels of pair q: jlo[q] <= j < jhi[q] (grouped by pair)
+  int mlo[4], mhi[4];            // channels whose two masks are both m (orbit kernel): mlo[m] <= j < mhi[m]
   unsigned long long wre[kMaxPassCh][16];  // (w.x, w.x) and (w.y, w.y) as packed FP32 pairs
   unsigned long long wim[kMaxPassCh][16];
 };
@@ -528,6 +530,291 @@ __global__ void __launch_bounds__(128) meson_fold_kernel(const double2* __restri
   }
 }
 
+
+// ---- orbit kernel: channels whose two masks are equal (ma == mb) -------------
+//
+// With ma = mb = m for every channel (the sixteen mesons Gamma_snk =
+// Gamma_src = Gamma(n) are of this kind: Gamma^dag permutes like Gamma), the
+// spin positions (alpha, beta) split into four orbits by d = alpha ^ beta,
+// and Q_m(alpha, alpha ^ d) pairs S1's block at (alpha, alpha ^ d) with S2's
+// block at (alpha ^ m, alpha ^ m ^ d), which lies in the same orbit.  A
+// thread owns (site, orbit d) for one first propagator: it keeps the orbit's
+// four 3x3 colour blocks of S_a in registers and streams the same orbit's
+// four blocks of each S_b once, each element serving all four masks.  The
+// four orbit threads of a site add their parts of each channel value through
+// shared memory.  One block stages OK_NP propagators for OK_S sites of one
+// timeslice with one tensor-map copy each (box: OK_S sites x 144
+// components, [comp][site] in shared memory).
+//
+// Pairs: first propagators ia in [0, NA) (staged index A[ia]) with second
+// propagators ib in [0, NB) (staged index B[ib]); site values of pair
+// (ia, ib) and channel j go to row rows[j] + (ia * NB + ib) * row_step.
+constexpr int kOrbMaxProps = 8;
+
+struct OrbitSet {
+  int np;                          // staged propagators
+  int na, nb;                      // first and second propagators in use (<= NA, NB)
+  int A[kOrbMaxProps], B[kOrbMaxProps];
+  int row_step;                    // SITES rows per pair (multi-propagator use)
+  int t0;                          // first timeslice of the launch (blockIdx.y = t - t0)
+  int nt_out;                      // timeslices of the site-value buffer
+  CUtensorMap map[kOrbMaxProps];   // staged propagators, box OK_S sites x 144 components
+};
+
+template <int NA, int NB, int OK_S, typename PsiT, bool SITES>
+__global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid_constant__ OrbitSet O, Geom g,
+                                                                     MesonPass P, Moms M, float2* __restrict__ sites,
+                                                                     const ScaleRecord* rec1, const ScaleRecord* rec2,
+                                                                     int site_scale, double2* __restrict__ partial,
+                                                                     unsigned int* status, long long timeout_ns) {
+  constexpr int kThreads = OK_S * 4 * NA;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  PsiT* st = reinterpret_cast<PsiT*>(smem_raw);  // [prop][144][OK_S]
+  constexpr uint32_t kPropBytes = 144u * OK_S * sizeof(PsiT);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)O.np * kPropBytes);
+  float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][NA][kMaxPassCh][OK_S] orbit parts
+  float2* cval = cpart + 4 * NA * kMaxPassCh * OK_S;      // [kMaxPassCh][OK_S] channel values (NA = NB = 1)
+  float2* phase = cval + kMaxPassCh * OK_S;               // [n_mom][OK_S]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // warp-uniform orbit: thread = ((d * NA) + ia) * OK_S + site
+  const int site = tid % OK_S, ia = (tid / OK_S) % NA, d = tid / (OK_S * NA);
+  const int s0 = blockIdx.x * OK_S, t = blockIdx.y;  // t: timeslice O.t0 + t of the lattice
+  const bool act = ia < O.na;                         // threads of an unused first propagator idle
+  const int s3 = s0 + site;
+  const bool live = s3 < g.V3;
+  const int V3 = g.V3;
+  const uint32_t bar_a = ptx::smem_addr(bar);
+
+  if (tid == 0) {
+    ptx::mbar_init(bar_a, 1);
+    ptx::fence_mbar_init();
+    ptx::mbar_arrive_expect_tx(bar_a, (uint32_t)O.np * kPropBytes);
+    for (int i = 0; i < O.np; ++i)
+      ptx::tensor_g2s_2d(ptx::smem_addr(smem_raw + (size_t)i * kPropBytes), &O.map[i], s0, (O.t0 + t) * 144, bar_a);
+  }
+  __syncthreads();
+  const bool ok = ptx::mbar_wait_bounded(bar_a, 0, timeout_ns);
+  if (!__syncthreads_and(ok ? 1 : 0)) {
+    if (tid == 0) {
+      atomicOr(status, kStatusFullWait);
+      if (!ptx::mbar_wait_bounded(bar_a, 0, timeout_ns)) atomicOr(status, kStatusDrain);
+    }
+    return;
+  }
+  // element (comp) of staged propagator i at this thread's site
+  auto elem = [&](int i, int comp) -> u64 {
+    return lds_pair_st(st + ((size_t)i * 144 + comp) * OK_S + site);
+  };
+  // component of (spin row al, spin column be, colour row c, colour column e)
+  auto comp_of = [](int al, int be, int c, int e) { return (al * 3 + c) * 12 + be * 3 + e; };
+
+  // this thread's orbit blocks of S_a: x[al][c*3+e] at (al, al ^ d)
+  u64 x[4][9];
+  const int pa = O.A[act ? ia : 0];
+#pragma unroll
+  for (int al = 0; al < 4; ++al)
+#pragma unroll
+    for (int k = 0; k < 9; ++k) x[al][k] = elem(pa, comp_of(al, al ^ d, k / 3, k % 3));
+
+  for (int ib = 0; ib < O.nb; ++ib) {
+    const int pb = O.B[ib];
+    // Pm[al][m] and Rm[al][m]: packed parts of Q_m(al, al ^ d) = sum x conj(y)
+    // for mask m = 0..3 (all four; every index compile-time), re = P.x + P.y,
+    // im = R.y - R.x
+    u64 Pm[4][4], Rm[4][4];
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) Pm[al][m] = Rm[al][m] = 0ull;
+#pragma unroll
+    for (int be = 0; be < 4; ++be) {  // S_b's orbit block at (be, be ^ d)
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const u64 y = live ? elem(pb, comp_of(be, be ^ d, k / 3, k % 3)) : 0ull;
+        const float2 yv = unpack2(y);
+        const u64 ys = pack2(yv.y, yv.x);
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {  // S1 block (al, al ^ d) pairs with S2 block (al ^ m, al ^ m ^ d)
+          const int al = be ^ m;
+          Pm[al][m] = fma2(x[al][k], y, Pm[al][m]);
+          Rm[al][m] = fma2(x[al][k], ys, Rm[al][m]);
+        }
+      }
+    }
+    // Q as (re, im) and i Q = (-im, re)
+    u64 Qz[4][4], Qi[4][4];
+#pragma unroll
+    for (int al = 0; al < 4; ++al)
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const float2 a = unpack2(Pm[al][m]), b = unpack2(Rm[al][m]);
+        const float re = a.x + a.y, im = b.y - b.x;
+        Qz[al][m] = pack2(re, im);
+        Qi[al][m] = pack2(-im, re);
+      }
+    // this orbit's part of every channel: sum_al w_j(al, al ^ d) Q_m(al, al ^ d)
+    // for the channels j of mask m (host-grouped: P.mlo[m] <= j < P.mhi[m])
+    if (act) {
+#pragma unroll
+      for (int m = 0; m < 4; ++m)
+        for (int j = P.mlo[m]; j < P.mhi[m]; ++j) {
+          u64 c = 0ull;
+#pragma unroll
+          for (int al = 0; al < 4; ++al) {
+            const int k = al * 4 + (al ^ d);
+            c = fma2(P.wre[j][k], Qz[al][m], c);
+            c = fma2(P.wim[j][k], Qi[al][m], c);
+          }
+          cpart[((d * NA + ia) * kMaxPassCh + j) * OK_S + site] = unpack2(c);
+        }
+    }
+    __syncthreads();
+    // the four orbits' parts of each (first propagator, channel, site), shared by all threads
+    const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
+    for (int u = tid; u < O.na * P.nch * OK_S; u += kThreads) {
+      const int us = u % OK_S, uj = (u / OK_S) % P.nch, ua = u / (OK_S * P.nch);
+      float2 c = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = 0; o < 4; ++o) {
+        const float2 v = cpart[((o * NA + ua) * kMaxPassCh + uj) * OK_S + us];
+        c.x += v.x;
+        c.y += v.y;
+      }
+      const int us3 = s0 + us;
+      if constexpr (SITES) {
+        if (us3 < V3) {
+          const long long row = (long long)P.out_row[uj] + (long long)(ua * O.nb + ib) * O.row_step;
+          sites[(row * O.nt_out + t) * V3 + us3] =
+              (scale_exp && site_scale) ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
+        }
+      } else {
+        cval[uj * OK_S + us] = us3 < V3 ? c : make_float2(0.f, 0.f);
+      }
+    }
+    __syncthreads();  // cpart is reused by the next second propagator
+  }
+  if constexpr (!SITES) {
+    // timeslice/momentum sums of the block's sites (NA = NB = 1): phases, then
+    // per value a warp's two-float butterfly over the OK_S sites
+    if (d == 1 && !M.zero_only) {
+      int c0 = 0, c1 = 0, c2 = 0;
+      if (live) {
+        c0 = s3 % g.sL[0];
+        c1 = (s3 / g.sL[0]) % g.sL[1];
+        c2 = s3 / (g.sL[0] * g.sL[1]);
+      }
+      for (int m = 0; m < M.n; ++m) {
+        long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
+                        (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
+                        (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
+        num %= V3;
+        if (num < 0) num += V3;
+        float sn, cs;
+        sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
+        phase[m * OK_S + site] = make_float2(cs, sn);
+      }
+    }
+    __syncthreads();
+    static_assert(SITES || OK_S == 32, "the reducing form takes 32 sites per block (one per lane)");
+    const int nv = P.nch * M.n;
+    for (int v = warp; v < nv; v += kThreads / 32) {
+      const int j = v / M.n, m = v % M.n;
+      float2 a = cval[j * OK_S + lane];
+      if (!M.zero_only) {
+        const float2 pa2 = phase[m * OK_S + lane];
+        a = make_float2(a.x * pa2.x + a.y * pa2.y, a.y * pa2.x - a.x * pa2.y);  // c (cs - i sn)
+      }
+      float2 hi = a, lo = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float hx = __shfl_xor_sync(0xffffffffu, hi.x, o), lx = __shfl_xor_sync(0xffffffffu, lo.x, o);
+        const float hy = __shfl_xor_sync(0xffffffffu, hi.y, o), ly = __shfl_xor_sync(0xffffffffu, lo.y, o);
+        float ex, ey;
+        two_sum(hi.x, hx, hi.x, ex);
+        two_sum(hi.y, hy, hi.y, ey);
+        lo.x = lo.x + lx + ex;
+        lo.y = lo.y + ly + ey;
+      }
+      if (lane == 0)
+        partial[((long long)t * gridDim.x + blockIdx.x) * nv + v] = make_double2((double)hi.x + (double)lo.x,
+                                                                                 (double)hi.y + (double)lo.y);
+    }
+  }
+}
+
+
+// The orbit kernel for one pass of one pair (S1, S2), or QDPG_ERR_UNSUPPORTED
+// where it does not apply (a channel with different masks, float16's
+// site-major layout, a component row not a multiple of 16 bytes, no
+// tensor-map support).
+int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
+                      float2* sites, cudaStream_t s, int site_scale) {
+  constexpr int kS = 32;
+  const Geom& g = S1->g;
+  const bool bf = S1->prec == QDPG_BF16;
+  if (S1->prec != QDPG_F32 && !bf) return QDPG_ERR_UNSUPPORTED;
+  for (int q = 0; q < P.nq; ++q)
+    if (P.ma[q] != P.mb[q]) return QDPG_ERR_UNSUPPORTED;
+  const int esize = bf ? 4 : 8;
+  if (((long long)g.V3 * esize) % 16 != 0) return QDPG_ERR_UNSUPPORTED;
+  const bool same = S1->data == S2->data;
+  OrbitSet O{};
+  O.np = same ? 1 : 2;
+  O.na = O.nb = 1;
+  O.A[0] = 0;
+  O.B[0] = same ? 0 : 1;
+  O.row_step = 0;
+  O.t0 = 0;
+  O.nt_out = g.Nt;
+  const qdpg_field* staged[2] = {S1, S2};
+  for (int i = 0; i < O.np; ++i)
+    if (reinterpret_cast<uintptr_t>(staged[i]->data) % 16 != 0 ||
+        !encode_map_2d(&O.map[i], staged[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
+                       (uint64_t)g.V3 * esize, kS, 144))
+      return QDPG_ERR_UNSUPPORTED;
+  unsigned int* status = device_status_word();
+  if (!status) return QDPG_ERR_UNSUPPORTED;
+  const size_t smem = (size_t)O.np * 144 * kS * esize + 16 + (size_t)4 * kMaxPassCh * kS * sizeof(float2) +
+                      (size_t)kMaxPassCh * kS * sizeof(float2) + (size_t)M.n * kS * sizeof(float2);
+  dim3 grid((g.V3 + kS - 1) / kS, g.Nt);
+  void* partial = nullptr;
+  if (!sites) {
+    const int arc = dev_alloc(&partial, sizeof(double2) * (size_t)grid.x * g.Nt * P.nch * M.n, s,
+                              "meson_2pt partial sums");
+    if (arc != QDPG_OK) return arc;
+  }
+  ProfScope prof("meson_2pt", s);
+  cudaError_t e = cudaSuccess;
+#define QDPG_ORBIT(T, SITES)                                                                                   \
+  do {                                                                                                         \
+    auto k = meson_orbit_kernel<1, 1, kS, T, SITES>;                                                           \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+    if (e == cudaSuccess)                                                                                      \
+      k<<<grid, kS * 4, smem, s>>>(O, g, P, M, sites, S1->rec, S2->rec, site_scale,                            \
+                                   static_cast<double2*>(partial), status, wait_timeout_ns());                  \
+  } while (0)
+  if (bf) {
+    if (sites) QDPG_ORBIT(__nv_bfloat162, true);
+    else QDPG_ORBIT(__nv_bfloat162, false);
+  } else {
+    if (sites) QDPG_ORBIT(float2, true);
+    else QDPG_ORBIT(float2, false);
+  }
+#undef QDPG_ORBIT
+  if (e != cudaSuccess) {
+    dev_free(partial, s);
+    return fail(QDPG_ERR_CUDA, "meson_2pt: smem attribute: %s", cudaGetErrorString(e));
+  }
+  int rc = check_launch("meson_2pt");
+  if (rc == QDPG_OK && !sites) {
+    meson_fold_kernel<<<dim3(P.nch * M.n, g.Nt), 128, 0, s>>>(static_cast<const double2*>(partial), (int)grid.x, P,
+                                                              M.n, g.Nt, out, S1->rec, S2->rec);
+    rc = check_launch("meson_2pt fold");
+  }
+  dev_free(partial, s);
+  return rc;
+}
+
 // The staged kernel for one pass, or QDPG_ERR_UNSUPPORTED where it does not
 // apply (float16's site-major layout; a component row of the timeslice not a
 // multiple of 16 bytes; no tensor-map support).
@@ -618,7 +905,12 @@ inline unsigned long long pack_host(float lo, float hi) {
 int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
                 float2* sites, cudaStream_t s, int site_scale = 1) {
   const Geom& g = S1->g;
-  if (!debug_meson_unstaged()) {
+  const int form = debug_meson_form();  // 0: best available, 1: staged, 2: global reads
+  if (form == 0) {
+    const int rc = launch_orbit_pass(P, M, S1, S2, out, sites, s, site_scale);
+    if (rc != QDPG_ERR_UNSUPPORTED) return rc;
+  }
+  if (form <= 1) {
     const int rc = launch_staged_pass(P, M, S1, S2, out, sites, s, site_scale);
     if (rc != QDPG_ERR_UNSUPPORTED) return rc;
   }
@@ -671,6 +963,56 @@ using namespace qdpg;
 namespace qdpg {
 namespace {
 
+
+// Channel masks and weights (the XOR-mask form of the trace, see the top of
+// this file), sorted by mask pair.
+int build_channels(const int* gamma_snk, const int* gamma_src, int n_chan, std::vector<Channel>& sorted,
+                   const char* who) {
+  static const int g5[4] = {1, 1, -1, -1};
+  std::vector<Channel> chans;
+  for (int j = 0; j < n_chan; ++j) {
+    if (gamma_snk[j] < 0 || gamma_snk[j] > 15 || gamma_src[j] < 0 || gamma_src[j] > 15)
+      return fail(QDPG_ERR_ARG, "%s: gamma index outside 0..15 in channel %d", who, j);
+    Mat4 A = Gamma(gamma_snk[j]);
+    Mat4 B = dagger(Gamma(gamma_src[j]));
+    Channel c{};
+    c.row = j;
+    c.ma = xor_mask(A);
+    c.mb = xor_mask(B);
+    if (c.ma < 0 || c.mb < 0) return fail(QDPG_ERR_ARG, "%s: internal gamma table error", who);
+    for (int al = 0; al < 4; ++al)
+      for (int be = 0; be < 4; ++be) {
+        CInt w = A.m[al ^ c.ma][al] * B.m[be][be ^ c.mb];
+        const int sgn = g5[be ^ c.mb] * g5[al ^ c.ma];
+        c.w[al * 4 + be] = make_float2((float)(sgn * w.re), (float)(sgn * w.im));
+      }
+    chans.push_back(c);
+  }
+  sorted.clear();
+  for (int pair = 0; pair < 16; ++pair)
+    for (const Channel& c : chans)
+      if (c.ma * 4 + c.mb == pair) sorted.push_back(c);
+  return QDPG_OK;
+}
+
+// Add channel c to pass P (pair index q); channels of one pair stay contiguous.
+void add_channel(MesonPass& P, int q, const Channel& c) {
+  P.q_of[P.nch] = q;
+  P.out_row[P.nch] = c.row;
+  for (int k = 0; k < 16; ++k) {
+    P.w[P.nch][k] = c.w[k];
+    P.wre[P.nch][k] = pack_host(c.w[k].x, c.w[k].x);
+    P.wim[P.nch][k] = pack_host(c.w[k].y, c.w[k].y);
+  }
+  ++P.nch;
+  if (P.jhi[q] == 0) P.jlo[q] = P.nch - 1;
+  P.jhi[q] = P.nch;
+  if (c.ma == c.mb) {  // channels arrive sorted by mask pair: those of (m, m) are contiguous
+    if (P.mhi[c.ma] == 0) P.mlo[c.ma] = P.nch - 1;
+    P.mhi[c.ma] = P.nch;
+  }
+}
+
 // Shared by the reducing entry point (out_dev) and the site-value one (sites).
 int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const int* gamma_src, int n_chan,
                  const int* moms, int n_mom, const int origin[4], double* out_dev, float2* sites, void* stream) {
@@ -693,31 +1035,10 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
   for (int m = 0; m < n_mom; ++m)
     for (int k = 0; k < 3; ++k) M.k[m][k] = moms[3 * m + k];
 
-  static const int g5[4] = {1, 1, -1, -1};
-  std::vector<Channel> chans;
-  for (int j = 0; j < n_chan; ++j) {
-    if (gamma_snk[j] < 0 || gamma_snk[j] > 15 || gamma_src[j] < 0 || gamma_src[j] > 15)
-      return fail(QDPG_ERR_ARG, "meson_2pt: gamma index outside 0..15 in channel %d", j);
-    Mat4 A = Gamma(gamma_snk[j]);
-    Mat4 B = dagger(Gamma(gamma_src[j]));
-    Channel c{};
-    c.row = j;
-    c.ma = xor_mask(A);
-    c.mb = xor_mask(B);
-    if (c.ma < 0 || c.mb < 0) return fail(QDPG_ERR_ARG, "meson_2pt: internal gamma table error");
-    for (int al = 0; al < 4; ++al)
-      for (int be = 0; be < 4; ++be) {
-        CInt w = A.m[al ^ c.ma][al] * B.m[be][be ^ c.mb];
-        const int sgn = g5[be ^ c.mb] * g5[al ^ c.ma];
-        c.w[al * 4 + be] = make_float2((float)(sgn * w.re), (float)(sgn * w.im));
-      }
-    chans.push_back(c);
-  }
-  // group channels by mask pair, then pack passes of <= 4 pairs and <= 16 channels
+  // channels grouped by mask pair, then packed into passes of <= 4 pairs and <= 16 channels
   std::vector<Channel> sorted;
-  for (int pair = 0; pair < 16; ++pair)
-    for (const Channel& c : chans)
-      if (c.ma * 4 + c.mb == pair) sorted.push_back(c);
+  const int crc = build_channels(gamma_snk, gamma_src, n_chan, sorted, "meson_2pt");
+  if (crc != QDPG_OK) return crc;
 
   cudaStream_t s = as_stream(stream);
   if (!sites) {
@@ -781,17 +1102,7 @@ int meson_common(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const i
       P.ma[q] = c.ma;
       P.mb[q] = c.mb;
     }
-    P.q_of[P.nch] = q;
-    P.out_row[P.nch] = c.row;
-    for (int k = 0; k < 16; ++k) {
-      P.w[P.nch][k] = c.w[k];
-      P.wre[P.nch][k] = pack_host(c.w[k].x, c.w[k].x);
-      P.wim[P.nch][k] = pack_host(c.w[k].y, c.w[k].y);
-    }
-    ++P.nch;
-    // channels arrive grouped by mask pair, so pair q's channels are contiguous
-    if (P.jhi[q] == 0) P.jlo[q] = P.nch - 1;
-    P.jhi[q] = P.nch;
+    add_channel(P, q, c);  // channels arrive grouped by mask pair
   }
   return flush();
 }
@@ -817,3 +1128,141 @@ int qdpg_meson_sites(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, con
 }
 
 }  // extern "C"
+
+// ---- all pairs of a set of propagators -------------------------------------
+
+namespace qdpg {
+namespace {
+
+struct RecTable {
+  const ScaleRecord* r[kOrbMaxProps];
+};
+// exp[(a * n + b) * n_chan + c] = exp_a + exp_b: the scale of pair (a, b)'s sums
+__global__ void pair_exp_kernel_t(RecTable R, int n, int n_chan, int* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n * n * n_chan) return;
+  const int pair = i / n_chan, a = pair / n, b = pair % n;
+  out[i] = R.r[a]->exp + R.r[b]->exp;
+}
+
+}  // namespace
+}  // namespace qdpg
+
+extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, const int* gamma_snk,
+                                    const int* gamma_src, int n_chan, const int* moms, int n_mom, const int origin[4],
+                                    double* out_dev, void* stream) {
+  constexpr int kS = 4;  // sites per block: 4 sites x 4 orbits x 8 first propagators = 128 threads
+  if (!props || !gamma_snk || !gamma_src || !moms || !out_dev) return fail(QDPG_ERR_ARG, "meson_2pt_multi: null argument");
+  if (n_props < 1 || n_props > kOrbMaxProps)
+    return fail(QDPG_ERR_ARG, "meson_2pt_multi: n_props %d outside 1..%d", n_props, kOrbMaxProps);
+  for (int i = 0; i < n_props; ++i) {
+    const qdpg_field* f = props[i];
+    if (!f) return fail(QDPG_ERR_ARG, "meson_2pt_multi: null propagator %d", i);
+    if (f->kind != QDPG_PROPAGATOR) return fail(QDPG_ERR_SHAPE, "meson_2pt_multi: field %d is not a propagator", i);
+    if (f->prec != QDPG_F32 && f->prec != QDPG_BF16)
+      return fail(QDPG_ERR_DTYPE, "meson_2pt_multi: propagators must be F32 or BF16 (field %d)", i);
+    if (f->prec != props[0]->prec) return fail(QDPG_ERR_DTYPE, "meson_2pt_multi: propagators differ in storage");
+    for (int mu = 0; mu < 4; ++mu)
+      if (f->g.L[mu] != props[0]->g.L[mu] || f->g.jd != props[0]->g.jd)
+        return fail(QDPG_ERR_SHAPE, "meson_2pt_multi: lattices differ");
+  }
+  if (n_chan < 1 || n_chan > kMaxPassCh)
+    return fail(QDPG_ERR_ARG, "meson_2pt_multi: n_chan %d outside 1..%d", n_chan, kMaxPassCh);
+  if (n_mom < 1 || n_mom > kMaxMom) return fail(QDPG_ERR_ARG, "meson_2pt_multi: n_mom %d outside 1..%d", n_mom, kMaxMom);
+  std::vector<Channel> sorted;
+  int rc = build_channels(gamma_snk, gamma_src, n_chan, sorted, "meson_2pt_multi");
+  if (rc != QDPG_OK) return rc;
+  MesonPass P{};
+  for (const Channel& c : sorted) {
+    if (c.ma != c.mb)
+      return fail(QDPG_ERR_UNSUPPORTED, "meson_2pt_multi: channel %d has unequal masks (only Gamma_snk, Gamma_src "
+                  "pairs that permute alike, such as Gamma_snk = Gamma_src)", c.row);
+    int q = -1;
+    for (int i = 0; i < P.nq; ++i)
+      if (P.ma[i] == c.ma) q = i;
+    if (q < 0) {
+      q = P.nq++;
+      P.ma[q] = P.mb[q] = c.ma;
+    }
+    add_channel(P, q, c);
+  }
+  const Geom& g = props[0]->g;
+  const bool bf = props[0]->prec == QDPG_BF16;
+  const int esize = bf ? 4 : 8;
+  if (((long long)g.V3 * esize) % 16 != 0)
+    return fail(QDPG_ERR_UNSUPPORTED, "meson_2pt_multi: a timeslice's component row must be a multiple of 16 bytes");
+  OrbitSet O{};
+  O.np = O.na = O.nb = n_props;
+  O.row_step = n_chan;
+  RecTable R{};
+  for (int i = 0; i < n_props; ++i) {
+    O.A[i] = O.B[i] = i;
+    R.r[i] = props[i]->rec;
+    if (reinterpret_cast<uintptr_t>(props[i]->data) % 16 != 0 ||
+        !encode_map_2d(&O.map[i], props[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
+                       (uint64_t)g.V3 * esize, kS, 144))
+      return fail(QDPG_ERR_UNSUPPORTED, "meson_2pt_multi: no tensor map for propagator %d", i);
+  }
+  unsigned int* status = device_status_word();
+  if (!status) return fail(QDPG_ERR_CUDA, "meson_2pt_multi: no status word");
+  Moms M{};
+  M.n = 1;
+  M.zero_only = true;
+  cudaStream_t s = as_stream(stream);
+
+  // timeslice batches: site values of all pairs and channels for up to 4 GiB
+  const long long n_rows = (long long)n_props * n_props * n_chan;
+  const size_t per_t = (size_t)n_rows * g.V3 * sizeof(float2);
+  int T = (int)std::min<long long>(g.Nt, std::max<long long>(1, (4LL << 30) / (long long)per_t));
+  void *sites = nullptr, *tout = nullptr, *cexp = nullptr;
+  rc = dev_alloc(&sites, per_t * T, s, "meson_2pt_multi site values");
+  if (rc == QDPG_OK) rc = dev_alloc(&tout, sizeof(double) * 2 * (size_t)n_rows * n_mom * T, s, "meson_2pt_multi sums");
+  if (rc == QDPG_OK) rc = dev_alloc(&cexp, sizeof(int) * (size_t)n_rows, s, "meson_2pt_multi scales");
+  if (rc == QDPG_OK) {
+    pair_exp_kernel_t<<<(int)((n_rows + 127) / 128), 128, 0, s>>>(R, n_props, n_chan, static_cast<int*>(cexp));
+    rc = check_launch("meson_2pt_multi scales");
+  }
+  const size_t smem = (size_t)n_props * 144 * kS * esize + 16 + (size_t)4 * kOrbMaxProps * kMaxPassCh * kS * sizeof(float2) +
+                      (size_t)kMaxPassCh * kS * sizeof(float2) + (size_t)M.n * kS * sizeof(float2);
+  std::vector<int> mom_flat(moms, moms + 3 * (size_t)n_mom);
+  for (int t0 = 0; t0 < g.Nt && rc == QDPG_OK; t0 += T) {
+    const int nt = std::min(T, g.Nt - t0);
+    O.t0 = t0;
+    O.nt_out = nt;
+    dim3 grid((g.V3 + kS - 1) / kS, nt);
+    cudaError_t e = cudaSuccess;
+    {
+      ProfScope prof("meson_2pt", s);
+#define QDPG_MULTI(T_)                                                                                          \
+  do {                                                                                                         \
+    auto k = meson_orbit_kernel<kOrbMaxProps, kOrbMaxProps, kS, T_, true>;                                     \
+    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
+    if (e == cudaSuccess)                                                                                      \
+      k<<<grid, kS * 4 * kOrbMaxProps, smem, s>>>(O, g, P, M, static_cast<float2*>(sites), nullptr, nullptr, 0, \
+                                                  nullptr, status, wait_timeout_ns());                          \
+  } while (0)
+      if (bf) QDPG_MULTI(__nv_bfloat162);
+      else QDPG_MULTI(float2);
+#undef QDPG_MULTI
+      if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "meson_2pt_multi: smem attribute: %s", cudaGetErrorString(e));
+      else rc = check_launch("meson_2pt_multi");
+    }
+    if (rc != QDPG_OK) break;
+    Geom gb = g;  // the batch as a lattice of nt timeslices for the projection's row layout
+    gb.Nt = nt;
+    gb.L[g.jd] = nt;
+    gb.V = (long long)nt * g.V3;
+    rc = launch_momproj(gb, sites, (int)n_rows, mom_flat.data(), n_mom, origin, static_cast<double*>(tout), nullptr,
+                        0, nullptr, 0, s, static_cast<const int*>(cexp));
+    if (rc != QDPG_OK) break;
+    // tout[row][m][0..nt) -> out[row][m][t0..t0+nt)
+    const cudaError_t ce = cudaMemcpy2DAsync(out_dev + 2 * (size_t)t0, sizeof(double) * 2 * g.Nt, tout,
+                                             sizeof(double) * 2 * nt, sizeof(double) * 2 * nt,
+                                             (size_t)n_rows * n_mom, cudaMemcpyDeviceToDevice, s);
+    if (ce != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "meson_2pt_multi: copy: %s", cudaGetErrorString(ce));
+  }
+  dev_free(sites, s);
+  dev_free(tout, s);
+  dev_free(cexp, s);
+  return rc;
+}

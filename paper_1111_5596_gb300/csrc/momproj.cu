@@ -27,7 +27,7 @@
 // its sites (the accumulator depth, at most kMaxCtaSites, bounds its
 // rounding) goes to a buffer of partial sums; a last kernel adds the CTAs'
 // partial sums in a fixed order in two-float arithmetic (error-free FP32
-// sums, FP64 once per output) and applies the fields' scale.
+// additions, FP64 once per output) and applies the fields' scale.
 #include <algorithm>
 
 #include "ptx.cuh"
@@ -42,7 +42,7 @@ constexpr int kM = 128;             // rows per CTA (tensor-core M)
 constexpr int kChunk = 16;          // sites per staged chunk
 constexpr int kKt = 2 * kChunk;     // real K per chunk
 constexpr int kMaxMomP = 64;        // N = 2*n_mom <= 128
-constexpr int kMaxCtaSites = 576;   // sites summed in one FP32 tensor-core accumulator
+constexpr int kMaxCtaSites = 256;   // sites summed in one FP32 tensor-core accumulator
 constexpr int kMaxL = 128;          // longest spatial extent of the phase tables
 
 struct ProjArgs {
@@ -286,19 +286,19 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 }
 
 // out[(chan * nmom + m) * Nt + t] = 2^e * sum over the site splits of the
-// partial sums: one warp per output, each lane a strided share of the
-// splits, all in two-float arithmetic (hi + lo), FP64 once at the end.
+// partial sums: one thread per output, consecutive threads on consecutive
+// rows (coalesced reads of partial[split][col][row] and writes of out), the
+// splits added in order in two-float arithmetic (hi + lo), FP64 once.
 __global__ void __launch_bounds__(256) momproj_fold_kernel(const float* __restrict__ partial, int nsplit, int rows,
                                                            int npad, int nmom, int Nt, double* __restrict__ out,
                                                            const ScaleRecord* ra, int ca, const ScaleRecord* rb,
-                                                           int cb) {
+                                                           int cb, const int* __restrict__ chan_exp) {
   const long long total = (long long)rows * nmom;
-  const long long w = blockIdx.x * 8LL + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (w >= total) return;
-  const int row = (int)(w % rows), m = (int)(w / rows);
+  const long long i = blockIdx.x * 256LL + threadIdx.x;
+  if (i >= total) return;
+  const int row = (int)(i % rows), m = (int)(i / rows);
   float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-  for (int sp = lane; sp < nsplit; sp += 32) {
+  for (int sp = 0; sp < nsplit; ++sp) {
     const float* p = partial + (size_t)sp * npad * rows;
     float e;
     two_sum(hr, p[(size_t)(2 * m) * rows + row], hr, e);
@@ -306,23 +306,11 @@ __global__ void __launch_bounds__(256) momproj_fold_kernel(const float* __restri
     two_sum(hi, p[(size_t)(2 * m + 1) * rows + row], hi, e);
     li += e;
   }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const float a = __shfl_xor_sync(0xffffffffu, hr, o), b = __shfl_xor_sync(0xffffffffu, lr, o);
-    const float c = __shfl_xor_sync(0xffffffffu, hi, o), d = __shfl_xor_sync(0xffffffffu, li, o);
-    float e;
-    two_sum(hr, a, hr, e);
-    lr += b + e;
-    two_sum(hi, c, hi, e);
-    li += d + e;
-  }
-  if (lane == 0) {
-    const int ex = (ra ? ca * ra->exp : 0) + (rb ? cb * rb->exp : 0);
-    const int chan = row / Nt, t = row % Nt;
-    const long long o = ((long long)chan * nmom + m) * Nt + t;
-    out[2 * o] = ldexp((double)hr + (double)lr, ex);
-    out[2 * o + 1] = ldexp((double)hi + (double)li, ex);
-  }
+  const int chan = row / Nt, t = row % Nt;
+  const int ex = chan_exp ? chan_exp[chan] : (ra ? ca * ra->exp : 0) + (rb ? cb * rb->exp : 0);
+  const long long o = ((long long)chan * nmom + m) * Nt + t;
+  out[2 * o] = ldexp((double)hr + (double)lr, ex);
+  out[2 * o + 1] = ldexp((double)hi + (double)li, ex);
 }
 
 }  // namespace
@@ -334,7 +322,8 @@ using namespace qdpg;
 namespace qdpg {
 
 int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* moms, int n_mom, const int origin[4],
-                   double* out_dev, const ScaleRecord* ra, int ca, const ScaleRecord* rb, int cb, cudaStream_t s) {
+                   double* out_dev, const ScaleRecord* ra, int ca, const ScaleRecord* rb, int cb, cudaStream_t s,
+                   const int* chan_exp) {
   if (n_chan < 1) return fail(QDPG_ERR_ARG, "momentum_project: n_chan %d < 1", n_chan);
   if (n_mom < 1 || n_mom > kMaxMomP) return fail(QDPG_ERR_ARG, "momentum_project: n_mom %d outside 1..%d", n_mom, kMaxMomP);
   if (reinterpret_cast<uintptr_t>(sites_dev) % 8) return fail(QDPG_ERR_ARG, "momentum_project: sites not 8-byte aligned");
@@ -399,9 +388,9 @@ int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* 
     }
     if (rc == QDPG_OK) {
       const long long nout = rows * n_mom;
-      momproj_fold_kernel<<<(int)((nout + 7) / 8), 256, 0, s>>>(static_cast<const float*>(partial), nsplit,
+      momproj_fold_kernel<<<(int)((nout + 255) / 256), 256, 0, s>>>(static_cast<const float*>(partial), nsplit,
                                                                   (int)rows, P.npad, n_mom, g.Nt, out_dev, ra, ca,
-                                                                  rb, cb);
+                                                                  rb, cb, chan_exp);
       rc = check_launch("momentum_project fold");
     }
   }

@@ -108,7 +108,7 @@ int debug_f16_warps();       // consumer warps of the float16 smearing kernel, 0
 // `what` on failure, including failures forced by QDPG_DEBUG_FAIL_ALLOCS.
 int dev_alloc(void** p, size_t bytes, cudaStream_t s, const char* what);
 long long debug_stage_bytes();  // chunk bound of the host-buffer import/export, 0 = default
-int debug_meson_unstaged();     // 1: meson contractions read S2 from global memory (no staging)
+int debug_meson_form();         // meson kernel: 0 best available, 1 staged S2, 2 global reads
 void dev_free(void* p, cudaStream_t s);
 constexpr unsigned int kStatusFullWait = 1u;   // consumer gave up waiting for data
 constexpr unsigned int kStatusEmptyWait = 2u;  // producer gave up waiting for a free stage
@@ -156,9 +156,11 @@ RescalePlan rescale_plan(double kappa, int n_iter);
 int launch_rescale(void* data, int prec, long long nelem, int shift, ScaleRecord* rec, cudaStream_t s);
 
 // Tensor-core momentum projection of site values (momproj.cu); the sums are
-// multiplied by 2^(ca * ra->exp + cb * rb->exp) (null records: 2^0).
+// multiplied by 2^(ca * ra->exp + cb * rb->exp) (null records: 2^0), or by
+// 2^chan_exp[chan] per channel where chan_exp (device memory) is given.
 int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* moms, int n_mom, const int origin[4],
-                   double* out_dev, const ScaleRecord* ra, int ca, const ScaleRecord* rb, int cb, cudaStream_t s);
+                   double* out_dev, const ScaleRecord* ra, int ca, const ScaleRecord* rb, int cb, cudaStream_t s,
+                   const int* chan_exp = nullptr);
 // meson_2pt/baryon_2pt with at least this many momenta project on the tensor cores.
 constexpr int kTensorProjMinMom = 8;
 

@@ -24,7 +24,7 @@ int g_f16_warps = 0;  // 0: the library's default (16)
 int g_tensor_copy_off = 0;  // 1: the pipelined hop stages with bulk copies only
 int g_fail_allocs = 0;      // the next this many device allocations fail (test hook)
 long long g_stage_bytes = 0;  // host import/export chunk bound, 0 = default
-int g_meson_unstaged = 0;     // 1: the meson contraction without the shared-memory staging
+int g_meson_form = 0;         // meson contraction kernel: 0 best available, 1 staged, 2 global reads
 std::atomic<uint64_t> g_allocs{0};
 
 }  // namespace
@@ -50,7 +50,7 @@ int debug_tile_grid() { return g_tile_grid; }
 int debug_f16_warps() { return g_f16_warps; }
 int debug_tensor_copy_off() { return g_tensor_copy_off; }
 long long debug_stage_bytes() { return g_stage_bytes; }
-int debug_meson_unstaged() { return g_meson_unstaged; }
+int debug_meson_form() { return g_meson_form; }
 
 // The library's memory pool on the current device, created on first use:
 // its own stream-ordered pool (not the device's default one), which keeps up
@@ -181,9 +181,9 @@ int qdpg_debug_set(int what, long long value) {
       if (value < 0 || value > (1LL << 40)) return fail(QDPG_ERR_ARG, "debug_set: staging bytes outside 0..2^40");
       g_stage_bytes = value;
       return ok();
-    case QDPG_DEBUG_MESON_UNSTAGED:
-      if (value < 0 || value > 1) return fail(QDPG_ERR_ARG, "debug_set: meson staging setting outside 0..1");
-      g_meson_unstaged = (int)value;
+    case QDPG_DEBUG_MESON_FORM:
+      if (value < 0 || value > 2) return fail(QDPG_ERR_ARG, "debug_set: meson kernel form outside 0..2");
+      g_meson_form = (int)value;
       return ok();
     case QDPG_DEBUG_FAIL_ALLOCS:
       if (value < 0 || value > 1000000) return fail(QDPG_ERR_ARG, "debug_set: failing allocations outside 0..1e6");

@@ -1,6 +1,9 @@
-"""The meson contraction with S2 staged in shared memory (the default for
-F32 and BF16 storage) against the same contraction reading S2 from global
-memory for every mask pair, and against the FP64 checker: zero and nonzero
+"""The three forms of the F32/BF16 meson contraction against each other and
+against the FP64 checker: the orbit kernel (the default where every
+channel's two masks are equal, as for the sixteen mesons: a thread keeps one
+orbit of spin blocks in registers), the kernel that stages S2 in shared
+memory (channels with unequal masks), and the one reading both propagators
+from global memory.  Channel sets with and without unequal masks; zero and nonzero
 momenta, site values, S1 = S2 and S1 != S2, a ragged last block (V3 not a
 multiple of the block's 64 sites) and another decay direction.  The two
 kernels split the sixteen weighted terms of a channel value differently,
@@ -23,16 +26,18 @@ def _prop(q, lat, seed, prec):
     return P, q.Field(lat, q.PROPAGATOR, q.PREC_NAMES[prec], device=DEV).import_(torch.from_numpy(P.astype(np.complex64)).to(DEV))
 
 
-def _both(q, fn):
-    a = fn()
-    q.debug_set(q.DEBUG_MESON_UNSTAGED, 1)
-    try:
-        b = fn()
-    finally:
-        q.debug_set(q.DEBUG_MESON_UNSTAGED, 0)
+def _forms(q, fn):
+    """The default kernel's result and those of the staged (1) and global-read (2) forms."""
+    out = []
+    for form in (0, 1, 2):
+        q.debug_set(q.DEBUG_MESON_FORM, form)
+        try:
+            out.append(fn().cpu().numpy())
+        finally:
+            q.debug_set(q.DEBUG_MESON_FORM, 0)
     torch.cuda.synchronize()
     q.device_status()
-    return a.cpu().numpy(), b.cpu().numpy()
+    return out
 
 
 CASES = [((8, 8, 8, 4), 3, "f32", True, ((0, 0, 0),)),
@@ -49,9 +54,9 @@ def test_staged_meson_matches_unstaged_and_checker(qdpg_gpu, dims, jd, prec, sam
     lat = q.Lattice(dims, jd)
     P1, S1 = _prop(q, lat, 3, prec)
     P2, S2 = (P1, S1) if same else _prop(q, lat, 4, prec)
-    chans = q.SIXTEEN_MESONS + ((1, 2), (5, 11), (15, 0))
-    a, b = _both(q, lambda: q.meson_2pt(S1, S2, chans, moms))
-    assert corr_err(a, b) <= 1e-6
+    chans = q.SIXTEEN_MESONS + ((1, 2), (5, 11), (15, 0)) if not same else q.SIXTEEN_MESONS
+    a, b, c = _forms(q, lambda: q.meson_2pt(S1, S2, chans, moms))
+    assert corr_err(a, c) <= 1e-6 and corr_err(b, c) <= 1e-6
     if prec == "f32":
         ref = hadron.meson_2pt(P1, P2, chans, moms, j_decay=jd)
         assert corr_err(a, ref) <= TOL_F32 if len(moms) < 8 else np.abs(a - ref).max() <= 1e-5 * np.abs(ref).max()
@@ -63,8 +68,8 @@ def test_staged_meson_site_values(qdpg_gpu):
     P1, S1 = _prop(q, lat, 5, "f32")
     P2, S2 = _prop(q, lat, 6, "f32")
     chans = q.SIXTEEN_MESONS
-    a, b = _both(q, lambda: q.meson_sites(S1, S2, chans))
-    assert np.abs(a - b).max() <= 1e-6 * np.abs(b).max()
+    a, b, c = _forms(q, lambda: q.meson_sites(S1, S2, chans))
+    assert np.abs(a - c).max() <= 1e-6 * np.abs(c).max() and np.abs(b - c).max() <= 1e-6 * np.abs(c).max()
     ref = np.stack([hadron.meson_site(P1, P2, x, y) for x, y in chans])       # (16, t, z, y, x)
     ref = ref.reshape(16, lat.Nt, lat.V3)
     assert np.abs(a - ref).max() <= 1e-6 * np.abs(ref).max()
