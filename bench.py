@@ -512,12 +512,7 @@ def scale_run(q, dev, args) -> dict:
         C = torch.empty((len(kn), len(kn), 16, len(moms), lat.Nt), dtype=torch.complex128, device=dev)
         e0, e1 = ev(), ev()
         e0.record()
-        if pp == q.F16:   # float16 (site-major) propagators: one pair at a time
-            for a in range(len(kn)):
-                for b in range(len(kn)):
-                    q.meson_2pt(props[a], props[b], q.SIXTEEN_MESONS, moms, out=C[a, b])
-        else:             # all 64 pairs in one pass: every propagator read once per site
-            q.meson_2pt_multi(props, q.SIXTEEN_MESONS, moms, out=C)
+        q.meson_2pt_multi(props, q.SIXTEEN_MESONS, moms, out=C)  # all 64 pairs: every propagator read once per site
         Cn = q.baryon_2pt(props[0], props[1], q.NUCLEON, +1, moms)
         e1.record()
         torch.cuda.synchronize()
@@ -526,8 +521,7 @@ def scale_run(q, dev, args) -> dict:
         corr[arm] = (C.cpu().numpy(), Cn.cpu().numpy())
         hops = sum(n for _, n in kn)
         res[arm] = {"smear_ms": t_smear, "contract_ms": t_con, "total_ms": t_smear + t_con, "hops": hops,
-                    "contraction": "qdpg_meson_2pt_multi (8 propagators, 64 pairs in one pass)" if pp != q.F16
-                    else "qdpg_meson_2pt per pair (64 calls)",
+                    "contraction": "qdpg_meson_2pt_multi (8 propagators, 64 pairs in one pass)",
                     "smear_gbs": hops * V * (2 * bpsi + blink) / (t_smear * 1e-3) / 1e9,
                     "smear_fp32_equiv_gbs": hops * V * 2520 / (t_smear * 1e-3) / 1e9,
                     "finite": bool(np.isfinite(corr[arm][0]).all() and np.isfinite(corr[arm][1]).all())}

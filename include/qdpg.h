@@ -367,7 +367,7 @@ int qdpg_meson_2pt(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, const
  * pairs and channels go, a batch of timeslices at a time (at most 4 GiB of
  * site values), to a library buffer and are projected on the tensor cores
  * (qdpg_momentum_project), each pair's sums multiplied by 2^(exp_a + exp_b).
- * props: 1..8 PROPAGATOR fields, all F32 or all BF16, same lattice.
+ * props: 1..8 PROPAGATOR fields, all F32, all BF16 or all F16, same lattice.
  * Channels: 1..16, each with Gamma_snk and Gamma_src that permute spin alike
  * (true for Gamma_snk = Gamma_src, as for the sixteen mesons; others return
  * QDPG_ERR_UNSUPPORTED).  moms, n_mom, origin as in qdpg_meson_2pt.

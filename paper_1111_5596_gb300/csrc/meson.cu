@@ -87,6 +87,10 @@ __device__ __forceinline__ u64 lds_pair_st(const __nv_bfloat162* p) {
   const float2 v = __bfloat1622float2(*p);
   return pack2(v.x, v.y);
 }
+__device__ __forceinline__ u64 lds_pair_st(const __half2* p) {
+  const float2 v = __half22float2(*p);
+  return pack2(v.x, v.y);
+}
 __device__ __forceinline__ float2 lds_elem(const float2* p) { return *p; }
 __device__ __forceinline__ float2 lds_elem(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
 __device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
@@ -569,7 +573,10 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
                                                                      unsigned int* status, long long timeout_ns) {
   constexpr int kThreads = OK_S * 4 * NA;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  PsiT* st = reinterpret_cast<PsiT*>(smem_raw);  // [prop][144][OK_S]
+  // F32/BF16: [prop][144 comps][OK_S sites]; float16 (site-major fields):
+  // [prop][3 vector groups][OK_S sites][48 words]
+  constexpr bool kF16 = std::is_same<PsiT, __half2>::value;
+  PsiT* st = reinterpret_cast<PsiT*>(smem_raw);
   constexpr uint32_t kPropBytes = 144u * OK_S * sizeof(PsiT);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)O.np * kPropBytes);
   float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][NA][kMaxPassCh][OK_S] orbit parts
@@ -589,8 +596,13 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
     ptx::mbar_init(bar_a, 1);
     ptx::fence_mbar_init();
     ptx::mbar_arrive_expect_tx(bar_a, (uint32_t)O.np * kPropBytes);
-    for (int i = 0; i < O.np; ++i)
-      ptx::tensor_g2s_2d(ptx::smem_addr(smem_raw + (size_t)i * kPropBytes), &O.map[i], s0, (O.t0 + t) * 144, bar_a);
+    for (int i = 0; i < O.np; ++i) {
+      if constexpr (kF16)
+        ptx::tensor_g2s_3d(ptx::smem_addr(smem_raw + (size_t)i * kPropBytes), &O.map[i], 0, s0, (O.t0 + t) * 3,
+                           bar_a);
+      else
+        ptx::tensor_g2s_2d(ptx::smem_addr(smem_raw + (size_t)i * kPropBytes), &O.map[i], s0, (O.t0 + t) * 144, bar_a);
+    }
   }
   __syncthreads();
   const bool ok = ptx::mbar_wait_bounded(bar_a, 0, timeout_ns);
@@ -603,7 +615,12 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
   }
   // element (comp) of staged propagator i at this thread's site
   auto elem = [&](int i, int comp) -> u64 {
-    return lds_pair_st(st + ((size_t)i * 144 + comp) * OK_S + site);
+    if constexpr (kF16) {
+      const int w = f16_site_word(comp);  // vector group * 48 + word
+      return lds_pair_st(st + (size_t)i * 144 * OK_S + ((w / 48) * OK_S + site) * 48 + w % 48);
+    } else {
+      return lds_pair_st(st + ((size_t)i * 144 + comp) * OK_S + site);
+    }
   };
   // component of (spin row al, spin column be, colour row c, colour column e)
   auto comp_of = [](int al, int be, int c, int e) { return (al * 3 + c) * 12 + be * 3 + e; };
@@ -1159,8 +1176,8 @@ extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, cons
     const qdpg_field* f = props[i];
     if (!f) return fail(QDPG_ERR_ARG, "meson_2pt_multi: null propagator %d", i);
     if (f->kind != QDPG_PROPAGATOR) return fail(QDPG_ERR_SHAPE, "meson_2pt_multi: field %d is not a propagator", i);
-    if (f->prec != QDPG_F32 && f->prec != QDPG_BF16)
-      return fail(QDPG_ERR_DTYPE, "meson_2pt_multi: propagators must be F32 or BF16 (field %d)", i);
+    if (f->prec != QDPG_F32 && f->prec != QDPG_BF16 && f->prec != QDPG_F16)
+      return fail(QDPG_ERR_DTYPE, "meson_2pt_multi: propagators must be F32, BF16 or F16 (field %d)", i);
     if (f->prec != props[0]->prec) return fail(QDPG_ERR_DTYPE, "meson_2pt_multi: propagators differ in storage");
     for (int mu = 0; mu < 4; ++mu)
       if (f->g.L[mu] != props[0]->g.L[mu] || f->g.jd != props[0]->g.jd)
@@ -1188,8 +1205,9 @@ extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, cons
   }
   const Geom& g = props[0]->g;
   const bool bf = props[0]->prec == QDPG_BF16;
-  const int esize = bf ? 4 : 8;
-  if (((long long)g.V3 * esize) % 16 != 0)
+  const bool h16 = props[0]->prec == QDPG_F16;
+  const int esize = bf || h16 ? 4 : 8;
+  if (!h16 && ((long long)g.V3 * esize) % 16 != 0)
     return fail(QDPG_ERR_UNSUPPORTED, "meson_2pt_multi: a timeslice's component row must be a multiple of 16 bytes");
   OrbitSet O{};
   O.np = O.na = O.nb = n_props;
@@ -1198,10 +1216,15 @@ extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, cons
   for (int i = 0; i < n_props; ++i) {
     O.A[i] = O.B[i] = i;
     R.r[i] = props[i]->rec;
-    if (reinterpret_cast<uintptr_t>(props[i]->data) % 16 != 0 ||
-        !encode_map_2d(&O.map[i], props[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
-                       (uint64_t)g.V3 * esize, kS, 144))
-      return fail(QDPG_ERR_UNSUPPORTED, "meson_2pt_multi: no tensor map for propagator %d", i);
+    // F32/BF16: (site; component row) boxes of kS x 144; float16: (word; site;
+    // timeslice-vector-group) boxes of 48 x kS x 3 (a site's 48 words of one group are contiguous)
+    const bool mapped =
+        reinterpret_cast<uintptr_t>(props[i]->data) % 16 == 0 &&
+        (h16 ? encode_map_3d(&O.map[i], props[i]->data, 4, 48, (uint64_t)g.V3, (uint64_t)g.Nt * 3, 48 * 4,
+                             (uint64_t)g.V3 * 48 * 4, 48, kS, 3)
+             : encode_map_2d(&O.map[i], props[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
+                             (uint64_t)g.V3 * esize, kS, 144));
+    if (!mapped) return fail(QDPG_ERR_UNSUPPORTED, "meson_2pt_multi: no tensor map for propagator %d", i);
   }
   unsigned int* status = device_status_word();
   if (!status) return fail(QDPG_ERR_CUDA, "meson_2pt_multi: no status word");
@@ -1241,7 +1264,8 @@ extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, cons
       k<<<grid, kS * 4 * kOrbMaxProps, smem, s>>>(O, g, P, M, static_cast<float2*>(sites), nullptr, nullptr, 0, \
                                                   nullptr, status, wait_timeout_ns());                          \
   } while (0)
-      if (bf) QDPG_MULTI(__nv_bfloat162);
+      if (h16) QDPG_MULTI(__half2);
+      else if (bf) QDPG_MULTI(__nv_bfloat162);
       else QDPG_MULTI(float2);
 #undef QDPG_MULTI
       if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "meson_2pt_multi: smem attribute: %s", cudaGetErrorString(e));

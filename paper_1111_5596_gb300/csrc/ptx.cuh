@@ -97,6 +97,15 @@ __device__ __forceinline__ void tensor_g2s_4d(uint32_t dst, const void* tmap, in
       : "memory");
 }
 
+// Tiled tensor copy global -> shared of one 3-D box (see tensor_g2s_4d).
+__device__ __forceinline__ void tensor_g2s_3d(uint32_t dst, const void* tmap, int c0, int c1, int c2, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];" ::"r"(dst),
+      "l"(tmap), "r"(c0), "r"(c1), "r"(c2), "r"(bar)
+      : "memory");
+}
+
 // Tiled tensor copy global -> shared of one 2-D box (see tensor_g2s_4d).
 __device__ __forceinline__ void tensor_g2s_2d(uint32_t dst, const void* tmap, int c0, int c1, uint32_t bar) {
   asm volatile(

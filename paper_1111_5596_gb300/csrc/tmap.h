@@ -17,4 +17,9 @@ namespace qdpg {
 bool encode_map_2d(CUtensorMap* m, const void* base, int esize, uint64_t dim0, uint64_t dim1, uint64_t row_bytes,
                    uint32_t box0, uint32_t box1);
 
+// A 3-D tiled map: dim0 x dim1 x dim2 elements, strides stride1 and stride2
+// bytes (multiples of 16) for dims 1 and 2, box box0 x box1 x box2.
+bool encode_map_3d(CUtensorMap* m, const void* base, int esize, uint64_t dim0, uint64_t dim1, uint64_t dim2,
+                   uint64_t stride1, uint64_t stride2, uint32_t box0, uint32_t box1, uint32_t box2);
+
 }  // namespace qdpg

@@ -2,7 +2,7 @@
 against the pairwise entry point and the FP64 checker: three propagators
 (one smeared far enough to be rescaled by its power-of-two scale record),
 the sixteen mesons at zero momentum and at the 33 momenta with |n|^2 <= 4,
-FP32 and BF16 storage, a lattice whose timeslice volume is not a multiple
+FP32, BF16 and float16 storage, a lattice whose timeslice volume is not a multiple
 of the kernel's 4-site blocks, and a timeslice batch smaller than the
 lattice (a tiny site-value budget is not settable, so a long Nt stands in:
 the batches are exercised by the 48^3x96 workload in the bench)."""
@@ -22,7 +22,8 @@ DEV = "cuda:0"
 def _props(q, dims, prec):
     lat = q.Lattice(dims, 3)
     U64 = fields.round_to_f32(fields.gauge_field(dims, 41, kind="haar"))
-    U = q.Field(lat, q.GAUGE, q.F32, device=DEV).import_(torch.from_numpy(U64.astype(np.complex64)).to(DEV))
+    lp = q.F16 if prec == "f16" else q.F32
+    U = q.Field(lat, q.GAUGE, lp, device=DEV).import_(torch.from_numpy(U64.astype(np.complex64)).to(DEV))
     out, ref = [], []
     for i, (kappa, n) in enumerate(((0.2, 3), (0.15, 1), (0.3, 60))):
         P64 = fields.round_to_f32(fields.propagator(dims, 41, field_id=10 + i, envelope=0.3))
@@ -35,7 +36,8 @@ def _props(q, dims, prec):
 
 
 @pytest.mark.parametrize("dims,prec,nmom", [((6, 5, 3, 4), "f32", 1), ((6, 5, 3, 4), "f32", 33),
-                                            ((8, 4, 4, 3), "bf16", 1), ((4, 4, 4, 6), "f32", 8)])
+                                            ((8, 4, 4, 3), "bf16", 1), ((4, 4, 4, 6), "f32", 8),
+                                            ((8, 6, 5, 3), "f16", 33), ((4, 5, 3, 4), "f16", 1)])
 def test_multi_equals_pairwise_and_checker(qdpg_gpu, dims, prec, nmom):
     q = qdpg_gpu
     lat, props, ref = _props(q, dims, prec)
