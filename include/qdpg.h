@@ -104,12 +104,24 @@ typedef enum {
 
 typedef enum {
   QDPG_F32 = 0,       /* complex float32 (float2) */
-  QDPG_BF16 = 1,      /* complex bfloat16 pair */
+  QDPG_BF16 = 1,      /* complex bfloat16 pair (see the accuracy note below) */
   QDPG_F32_R12 = 2,   /* gauge only: float2, two rows stored */
   QDPG_BF16_R12 = 3,  /* gauge only: bfloat16 pair, two rows stored */
   QDPG_F16 = 4,       /* complex float16 pair; propagator or gauge (layout notes above) */
   QDPG_F16_R12 = 5    /* gauge only: float16 pair, two rows stored */
 } qdpg_prec;
+
+/* Accuracy of the reduced-precision storages (measured against the FP32
+ * path, which agrees with an FP64 computation to ~1e-6):
+ *  - QDPG_F16 propagators with F16 / F16_R12 links (per-field power-of-two
+ *    scale, tensor-core hop): zero-momentum meson correlators within 4e-3 on
+ *    uneven smearing jobs with N up to 50 and kappa up to 0.30, and within
+ *    2.5e-3 on the 48^3x96 workload (N up to 80): inside a 2e-2 bound;
+ *  - QDPG_BF16 propagators with BF16 reconstruct-12 links: 1-2% on the
+ *    24^3x48 workload (N = 40, kappa = 0.21), but up to 3.2e-2 on uneven jobs
+ *    of the same N and kappa range, already 1% at N = 5 (the 8-bit links
+ *    dominate): BF16 storage does NOT hold a 2e-2 bound in general; use F16
+ *    storage where that bound must hold. */
 
 /* Size of the scale record of a propagator or fermion (see the layout
  * notes): int32 exp, float max |stored|, then the per-iteration scale slots

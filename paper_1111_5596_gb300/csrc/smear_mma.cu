@@ -32,8 +32,9 @@
 // work items (tile of k plane rows at (t, z)); one producer warp streams,
 // with bulk asynchronous copies, the tile's links and then per stage one
 // vector group of the tile, its y halo rows and the same rows of planes
-// z -+ 1; eight consumer warps each own up to eight sites of the tile and
-// keep their link fragments in registers for the item's three stages.
+// z -+ 1; sixteen consumer warps (the default; eight with the tuning
+// setting) each own four sites of the tile (eight with eight warps) and keep
+// their link fragments in registers for the item's three stages.
 // Every wait is bounded and reports through the device status word.
 #include <cuda_fp16.h>
 
