@@ -579,7 +579,7 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
   PsiT* st = reinterpret_cast<PsiT*>(smem_raw);
   constexpr uint32_t kPropBytes = 144u * OK_S * sizeof(PsiT);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)O.np * kPropBytes);
-  float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][NA][kMaxPassCh][OK_S] orbit parts
+  float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][kMaxPassCh][NA][OK_S] orbit parts
   float2* cval = cpart + 4 * NA * kMaxPassCh * OK_S;      // [kMaxPassCh][OK_S] channel values (NA = NB = 1)
   float2* phase = cval + kMaxPassCh * OK_S;               // [n_mom][OK_S]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -682,18 +682,19 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
             c = fma2(P.wre[j][k], Qz[al][m], c);
             c = fma2(P.wim[j][k], Qi[al][m], c);
           }
-          cpart[((d * NA + ia) * kMaxPassCh + j) * OK_S + site] = unpack2(c);
+          cpart[((d * kMaxPassCh + j) * NA + ia) * OK_S + site] = unpack2(c);  // a warp's lanes: contiguous
         }
     }
     __syncthreads();
     // the four orbits' parts of each (first propagator, channel, site), shared by all threads
     const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
-    for (int u = tid; u < O.na * P.nch * OK_S; u += kThreads) {
-      const int us = u % OK_S, uj = (u / OK_S) % P.nch, ua = u / (OK_S * P.nch);
+    for (int u = tid; u < P.nch * NA * OK_S; u += kThreads) {
+      const int us = u % OK_S, ua = (u / OK_S) % NA, uj = u / (OK_S * NA);
+      if (ua >= O.na) continue;
       float2 c = make_float2(0.f, 0.f);
 #pragma unroll
       for (int o = 0; o < 4; ++o) {
-        const float2 v = cpart[((o * NA + ua) * kMaxPassCh + uj) * OK_S + us];
+        const float2 v = cpart[((o * kMaxPassCh + uj) * NA + ua) * OK_S + us];
         c.x += v.x;
         c.y += v.y;
       }
