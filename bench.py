@@ -865,6 +865,26 @@ def gpu_arm(args):
         cpu = cpu_baseline(w, args.cpu_seconds)
 
     if rank == 0:
+        highlights = {"hop_16x32_us_per_launch": roofline["avg_launch_us"], "hop_16x32_hbm_frac": roofline["frac"],
+                      "hop_16x32_hbm_frac_back_to_back": roofline["frac_back_to_back"],
+                      "meson_2pt_16x32_p0_us": mes_ms / mes_n * 1e3, "meson_2pt_gbs": components["contraction_gbs"]}
+        if "hop_24x48" in components:
+            highlights["hop_24x48_us_per_launch"] = components["hop_24x48"]["avg_launch_us"]
+            highlights["hop_24x48_hbm_frac"] = components["hop_24x48"]["frac"]
+        if batch:
+            fl = batch.get("f16_full_links", {})
+            highlights.update({
+                "batch64_f16_vs_fp32_one_job": fl.get("speedup_vs_fp32_single"),
+                "batch64_f16_r12_vs_fp32_one_job": batch.get("speedup_f16_tc_batched_vs_fp32_single"),
+                "batch64_f16_corr_rel_err_max": fl.get("corr_rel_err_max"),
+                "batch64_f16_within_2e-2": fl.get("within_tol")})
+        sc48 = components.get("scale_48x96")
+        if sc48:
+            highlights.update({
+                "scale48_f16_vs_fp32_end_to_end": sc48.get("speedup_f16_tc_vs_fp32"),
+                "scale48_fp32_contract_ms": sc48.get("fp32", {}).get("contract_ms"),
+                "scale48_f16_contract_ms": sc48.get("f16_tc", {}).get("contract_ms"),
+                "scale48_fp32_vs_checker_p0_rel_err": sc48.get("fp32_vs_checker", {}).get("p0_corr_rel_err")})
         line = {
             "metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
@@ -874,7 +894,7 @@ def gpu_arm(args):
                     "exp(-0.5|x|) envelope, complex64",
             "config": dict(config_block(w), **({"parallelism": f"tslab{world}: one lattice in timeslice slabs, "
                                                                   "correlators gathered (NCCL all_gather) every step"}
-                                                 if tslab_mode else {})), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                                                 if tslab_mode else {})), "highlights": highlights, "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": clk, "components": components,
         }
         print(json.dumps(line), flush=True)
