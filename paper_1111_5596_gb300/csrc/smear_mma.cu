@@ -34,7 +34,10 @@
 // vector group of the tile, its y halo rows and the same rows of planes
 // z -+ 1; sixteen consumer warps (the default; eight with the tuning
 // setting) each own four sites of the tile (eight with eight warps) and keep
-// their link fragments in registers for the item's three stages.
+// their link fragments in registers for the item's three stages.  The
+// producer also writes the item's position into shared memory before it
+// signals the links, so the consumers do not decode item indices, and each
+// consumer computes its sites' stage offsets once (the tile shape is fixed).
 // Every wait is bounded and reports through the device status word.
 #include <cuda_fp16.h>
 
@@ -139,6 +142,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
   uint32_t* lb = st + (size_t)S * stage_words;
   int* tab = reinterpret_cast<int*>(lb + tt.link_words);
   uint64_t* bars = reinterpret_cast<uint64_t*>(tab + T * kTab);
+  int* hdr = reinterpret_cast<int*>(bars + 2 * S + 4);  // job, t, z, y0 of the item whose links are staged
   const uint32_t full0 = ptx::smem_addr(bars);
   const uint32_t empty0 = ptx::smem_addr(bars + S);
   const uint32_t lfull = ptx::smem_addr(bars + 2 * S);
@@ -202,7 +206,10 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
           break;
         }
       }
-      if (lane == 0) ptx::mbar_arrive_expect_tx(lfull, link_bytes);
+      if (lane == 0) {
+        hdr[0] = p.job; hdr[1] = p.t; hdr[2] = p.z; hdr[3] = p.y0;
+        ptx::mbar_arrive_expect_tx(lfull, link_bytes);
+      }
       __syncwarp();
       const uint32_t* Ut = J.j[p.job].U + (size_t)p.t * NCL * V3;
       for (int cp = lane; cp < nlcopies; cp += 32) {
@@ -303,11 +310,28 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
   const int nsw = (T - warp + kConsumerWarps - 1) / kConsumerWarps;
   ptx::wait_dependencies();  // the previous hop's spinors and scale slots
 
+  // per site: stage offsets (own, +-x, +-y, +-z), the same for every item
+  // (below 2^16 words: two per register)
+  uint32_t off[kSPW][4];
+#pragma unroll
+  for (int si = 0; si < kSPW; ++si) {
+    int sti = warp + si * kConsumerWarps;
+    sti = sti < T ? sti : T - 1;
+    const int* e = tab + sti * kTab;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) off[si][q] = (uint32_t)e[2 * q] | (q < 3 ? (uint32_t)e[2 * q + 1] << 16 : 0u);
+  }
   int cur_job = -1;
   float sc = 1.f, kap = 0.f, mx = 0.f;
   int s = 0, n = 0, nitem = 0;
   for (int it = blockIdx.x; it < total; it += gridDim.x, ++nitem) {
-    const ItemPos p = decode(it, tt, Lz);
+    bool ok = ptx::mbar_wait_bounded(lfull, nitem & 1, timeout_ns);
+    if (!__all_sync(0xffffffffu, ok)) {
+      if (lane == 0) atomicOr(status, kStatusFullWait);
+      return;
+    }
+    ItemPos p;
+    p.job = hdr[0]; p.t = hdr[1]; p.z = hdr[2]; p.y0 = hdr[3];
     if (p.job != cur_job) {
       if (cur_job >= 0) {
 #pragma unroll
@@ -322,11 +346,6 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
       const int d = delta_for(rec->cmax[iter], kap);
       sc = ldexpf(1.f, -d);
       if (it == p.job * tt.nitems && threadIdx.x == 0) J.j[p.job].rec->cexp[iter + 1] = rec->cexp[iter] + d;
-    }
-    bool ok = ptx::mbar_wait_bounded(lfull, nitem & 1, timeout_ns);
-    if (!__all_sync(0xffffffffu, ok)) {
-      if (lane == 0) atomicOr(status, kStatusFullWait);
-      return;
     }
     if (NE == 6) {
       // reconstruct row 2 of every staged link: row2 = (row0 x row1)^*
@@ -357,18 +376,14 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
         return;
       }
     }
-    // per site: stage offsets (own, +-x, +-y, +-z) and link fragments B_i
+    // per site: link fragments B_i
     // (forward M = U: (Mr, -Mi) | (Mi, Mr); backward M = conj(U^T): (Ur, Ui) | (-Ui, Ur))
-    // (stage offsets are below 2^16 words: two per register)
-    uint32_t off[kSPW][4];
     uint32_t bf[kSPW][3][2];
 #pragma unroll
     for (int si = 0; si < kSPW; ++si) {
       int sti = warp + si * kConsumerWarps;
       sti = sti < T ? sti : T - 1;
       const int* e = tab + sti * kTab;
-#pragma unroll
-      for (int q = 0; q < 4; ++q) off[si][q] = (uint32_t)e[2 * q] | (q < 3 ? (uint32_t)e[2 * q + 1] << 16 : 0u);
       const int bs1 = e[9];
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
@@ -490,12 +505,12 @@ bool pick_tile(const Geom& g, int ne, int njobs, Tile& tt) {
   const size_t stage_bytes = (size_t)tt.rows * Lx * kWords * 4;
   const size_t fixed = (size_t)tt.link_words * 4 + (size_t)tt.T * kTab * 4;
   const size_t budget = 225 * 1024;
-  const size_t bar_bytes = (2 * kMaxStages + 4) * 8;
+  const size_t bar_bytes = (2 * kMaxStages + 4) * 8 + 16;
   if (fixed + 2 * stage_bytes + bar_bytes > budget) return false;
   int S = (int)((budget - fixed - bar_bytes) / stage_bytes);
   if (S > kMaxStages) S = kMaxStages;
   tt.stages = S;
-  tt.smem = (int)(S * stage_bytes + fixed + (2 * S + 4) * 8);
+  tt.smem = (int)(S * stage_bytes + fixed + (2 * S + 4) * 8 + 16);
   tt.nitems = tt.ntiles_y * g.sL[2] * g.Nt;
   const int nsm = sm_count();
   if (nsm <= 0) return false;
