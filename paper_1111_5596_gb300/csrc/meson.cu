@@ -565,7 +565,7 @@ struct OrbitSet {
   CUtensorMap map[kOrbMaxProps];   // staged propagators, box OK_S sites x 144 components
 };
 
-template <int NA, int NB, int OK_S, typename PsiT, bool SITES>
+template <int NA, int NB, int OK_S, typename PsiT, bool SITES, bool SAME = false>
 __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid_constant__ OrbitSet O, Geom g,
                                                                      MesonPass P, Moms M, float2* __restrict__ sites,
                                                                      const ScaleRecord* rec1, const ScaleRecord* rec2,
@@ -580,9 +580,8 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
   constexpr uint32_t kPropBytes = 144u * OK_S * sizeof(PsiT);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)O.np * kPropBytes);
   float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][kMaxPassCh][NA][OK_S] orbit parts
-  float2* cval = cpart + 4 * NA * kMaxPassCh * OK_S;      // [kMaxPassCh][OK_S] channel values (NA = NB = 1)
-  float2* phase = cval + kMaxPassCh * OK_S;               // [n_mom][OK_S]
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  float2* phase = cpart + 4 * NA * kMaxPassCh * OK_S;     // [n_mom][OK_S] (reducing form)
+  const int tid = threadIdx.x;
   // warp-uniform orbit: thread = ((d * NA) + ia) * OK_S + site
   const int site = tid % OK_S, ia = (tid / OK_S) % NA, d = tid / (OK_S * NA);
   const int s0 = blockIdx.x * OK_S, t = blockIdx.y;  // t: timeslice O.t0 + t of the lattice
@@ -625,6 +624,28 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
   // component of (spin row al, spin column be, colour row c, colour column e)
   auto comp_of = [](int al, int be, int c, int e) { return (al * 3 + c) * 12 + be * 3 + e; };
 
+  if constexpr (!SITES) {
+    // phases of the block's sites for the momentum sums, read after the
+    // barrier that follows the orbit parts
+    if (d == 1 && !M.zero_only) {
+      int c0 = 0, c1 = 0, c2 = 0;
+      if (live) {
+        c0 = s3 % g.sL[0];
+        c1 = (s3 / g.sL[0]) % g.sL[1];
+        c2 = s3 / (g.sL[0] * g.sL[1]);
+      }
+      for (int m = 0; m < M.n; ++m) {
+        long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
+                        (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
+                        (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
+        num %= V3;
+        if (num < 0) num += V3;
+        float sn, cs;
+        sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
+        phase[m * OK_S + site] = make_float2(cs, sn);
+      }
+    }
+  }
   // this thread's orbit blocks of S_a: x[al][c*3+e] at (al, al ^ d)
   u64 x[4][9];
   const int pa = O.A[act ? ia : 0];
@@ -635,6 +656,58 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
 
   for (int ib = 0; ib < O.nb; ++ib) {
     const int pb = O.B[ib];
+    // Q as (re, im) and i Q = (-im, re)
+    u64 Qz[4][4], Qi[4][4];
+    if constexpr (SAME) {
+      // S2 = S1: S2's orbit blocks are this thread's x, and
+      // Q_m(al ^ m, .) = conj(Q_m(al, .)): |x|^2 sums for m = 0 and one
+      // product per pair {al, al ^ m} (al the smaller) for m = 1, 2, 3
+      (void)pb;
+      u64 P0[4], Pp[3][2], Rp[3][2];
+#pragma unroll
+      for (int al = 0; al < 4; ++al) P0[al] = 0ull;
+#pragma unroll
+      for (int m = 1; m < 4; ++m) Pp[m - 1][0] = Pp[m - 1][1] = Rp[m - 1][0] = Rp[m - 1][1] = 0ull;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        u64 xs[4];
+#pragma unroll
+        for (int b = 1; b < 4; ++b) {
+          const float2 v = unpack2(x[b][k]);
+          xs[b] = pack2(v.y, v.x);
+        }
+#pragma unroll
+        for (int al = 0; al < 4; ++al) P0[al] = fma2(x[al][k], x[al][k], P0[al]);
+#pragma unroll
+        for (int m = 1; m < 4; ++m)
+#pragma unroll
+          for (int q = 0; q < 2; ++q) {
+            // the pair's smaller member: m = 1: 0, 2; m = 2: 0, 1; m = 3: 0, 1
+            const int lo = m == 1 ? 2 * q : q, hi = lo ^ m;
+            Pp[m - 1][q] = fma2(x[lo][k], x[hi][k], Pp[m - 1][q]);
+            Rp[m - 1][q] = fma2(x[lo][k], xs[hi], Rp[m - 1][q]);
+          }
+      }
+#pragma unroll
+      for (int al = 0; al < 4; ++al) {
+        const float2 a = unpack2(P0[al]);
+        const float re = a.x + a.y;
+        Qz[al][0] = pack2(re, 0.f);
+        Qi[al][0] = pack2(0.f, re);
+      }
+#pragma unroll
+      for (int m = 1; m < 4; ++m)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int lo = m == 1 ? 2 * q : q, hi = lo ^ m;
+          const float2 a = unpack2(Pp[m - 1][q]), b = unpack2(Rp[m - 1][q]);
+          const float re = a.x + a.y, im = b.y - b.x;
+          Qz[lo][m] = pack2(re, im);
+          Qi[lo][m] = pack2(-im, re);
+          Qz[hi][m] = pack2(re, -im);
+          Qi[hi][m] = pack2(im, re);
+        }
+    } else {
     // Pm[al][m] and Rm[al][m]: packed parts of Q_m(al, al ^ d) = sum x conj(y)
     // for mask m = 0..3 (all four; every index compile-time), re = P.x + P.y,
     // im = R.y - R.x
@@ -658,8 +731,6 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
         }
       }
     }
-    // Q as (re, im) and i Q = (-im, re)
-    u64 Qz[4][4], Qi[4][4];
 #pragma unroll
     for (int al = 0; al < 4; ++al)
 #pragma unroll
@@ -669,6 +740,7 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
         Qz[al][m] = pack2(re, im);
         Qi[al][m] = pack2(-im, re);
       }
+    }
     // this orbit's part of every channel: sum_al w_j(al, al ^ d) Q_m(al, al ^ d)
     // for the channels j of mask m (host-grouped: P.mlo[m] <= j < P.mhi[m])
     if (act) {
@@ -686,77 +758,78 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
         }
     }
     __syncthreads();
-    // the four orbits' parts of each (first propagator, channel, site), shared by all threads
-    const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
-    for (int u = tid; u < P.nch * NA * OK_S; u += kThreads) {
-      const int us = u % OK_S, ua = (u / OK_S) % NA, uj = u / (OK_S * NA);
-      if (ua >= O.na) continue;
-      float2 c = make_float2(0.f, 0.f);
+    if constexpr (SITES) {
+      // the four orbits' parts of each (first propagator, channel, site), shared by all threads
+      const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
+      for (int u = tid; u < P.nch * NA * OK_S; u += kThreads) {
+        const int us = u % OK_S, ua = (u / OK_S) % NA, uj = u / (OK_S * NA);
+        if (ua >= O.na) continue;
+        float2 c = make_float2(0.f, 0.f);
 #pragma unroll
-      for (int o = 0; o < 4; ++o) {
-        const float2 v = cpart[((o * kMaxPassCh + uj) * NA + ua) * OK_S + us];
-        c.x += v.x;
-        c.y += v.y;
-      }
-      const int us3 = s0 + us;
-      if constexpr (SITES) {
+        for (int o = 0; o < 4; ++o) {
+          const float2 v = cpart[((o * kMaxPassCh + uj) * NA + ua) * OK_S + us];
+          c.x += v.x;
+          c.y += v.y;
+        }
+        const int us3 = s0 + us;
         if (us3 < V3) {
           const long long row = (long long)P.out_row[uj] + (long long)(ua * O.nb + ib) * O.row_step;
           sites[(row * O.nt_out + t) * V3 + us3] =
               (scale_exp && site_scale) ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
         }
-      } else {
-        cval[uj * OK_S + us] = us3 < V3 ? c : make_float2(0.f, 0.f);
+      }
+    } else {
+      // timeslice/momentum sums of the block's sites (NA = NB = 1): thread
+      // (channel tid / 8, sites 4 (tid % 8) .. +3) adds the four orbits'
+      // parts of its sites, multiplies them by the phases and sums them in
+      // two-float arithmetic; the channel's eight lanes finish each sum
+      // with a three-step butterfly
+      static_assert(SITES || (OK_S == 32 && NA == 1), "the reducing form takes one pair and 32 sites per block");
+      const int uj = tid >> 3, g4 = (tid & 7) * 4;
+      const int nv = P.nch * M.n;
+      float2 cs[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        float2 c = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) {
+          const float2 v = cpart[(o * kMaxPassCh + uj) * OK_S + g4 + q];
+          c.x += v.x;
+          c.y += v.y;
+        }
+        cs[q] = (uj < P.nch && s0 + g4 + q < V3) ? c : make_float2(0.f, 0.f);
+      }
+      for (int m = 0; m < M.n; ++m) {
+        float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          float2 a = cs[q];
+          if (!M.zero_only) {
+            const float2 pa2 = phase[m * OK_S + g4 + q];
+            a = make_float2(a.x * pa2.x + a.y * pa2.y, a.y * pa2.x - a.x * pa2.y);  // c (cs - i sn)
+          }
+          float ex, ey;
+          two_sum(hi.x, a.x, hi.x, ex);
+          two_sum(hi.y, a.y, hi.y, ey);
+          lo.x += ex;
+          lo.y += ey;
+        }
+#pragma unroll
+        for (int o = 4; o > 0; o >>= 1) {
+          const float hx = __shfl_xor_sync(0xffffffffu, hi.x, o), lx = __shfl_xor_sync(0xffffffffu, lo.x, o);
+          const float hy = __shfl_xor_sync(0xffffffffu, hi.y, o), ly = __shfl_xor_sync(0xffffffffu, lo.y, o);
+          float ex, ey;
+          two_sum(hi.x, hx, hi.x, ex);
+          two_sum(hi.y, hy, hi.y, ey);
+          lo.x = lo.x + lx + ex;
+          lo.y = lo.y + ly + ey;
+        }
+        if ((tid & 7) == 0 && uj < P.nch)
+          partial[((long long)t * gridDim.x + blockIdx.x) * nv + uj * M.n + m] =
+              make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
       }
     }
     __syncthreads();  // cpart is reused by the next second propagator
-  }
-  if constexpr (!SITES) {
-    // timeslice/momentum sums of the block's sites (NA = NB = 1): phases, then
-    // per value a warp's two-float butterfly over the OK_S sites
-    if (d == 1 && !M.zero_only) {
-      int c0 = 0, c1 = 0, c2 = 0;
-      if (live) {
-        c0 = s3 % g.sL[0];
-        c1 = (s3 / g.sL[0]) % g.sL[1];
-        c2 = s3 / (g.sL[0] * g.sL[1]);
-      }
-      for (int m = 0; m < M.n; ++m) {
-        long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
-                        (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
-                        (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
-        num %= V3;
-        if (num < 0) num += V3;
-        float sn, cs;
-        sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
-        phase[m * OK_S + site] = make_float2(cs, sn);
-      }
-    }
-    __syncthreads();
-    static_assert(SITES || OK_S == 32, "the reducing form takes 32 sites per block (one per lane)");
-    const int nv = P.nch * M.n;
-    for (int v = warp; v < nv; v += kThreads / 32) {
-      const int j = v / M.n, m = v % M.n;
-      float2 a = cval[j * OK_S + lane];
-      if (!M.zero_only) {
-        const float2 pa2 = phase[m * OK_S + lane];
-        a = make_float2(a.x * pa2.x + a.y * pa2.y, a.y * pa2.x - a.x * pa2.y);  // c (cs - i sn)
-      }
-      float2 hi = a, lo = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float hx = __shfl_xor_sync(0xffffffffu, hi.x, o), lx = __shfl_xor_sync(0xffffffffu, lo.x, o);
-        const float hy = __shfl_xor_sync(0xffffffffu, hi.y, o), ly = __shfl_xor_sync(0xffffffffu, lo.y, o);
-        float ex, ey;
-        two_sum(hi.x, hx, hi.x, ex);
-        two_sum(hi.y, hy, hi.y, ey);
-        lo.x = lo.x + lx + ex;
-        lo.y = lo.y + ly + ey;
-      }
-      if (lane == 0)
-        partial[((long long)t * gridDim.x + blockIdx.x) * nv + v] = make_double2((double)hi.x + (double)lo.x,
-                                                                                 (double)hi.y + (double)lo.y);
-    }
   }
 }
 
@@ -793,7 +866,7 @@ int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, c
   unsigned int* status = device_status_word();
   if (!status) return QDPG_ERR_UNSUPPORTED;
   const size_t smem = (size_t)O.np * 144 * kS * esize + 16 + (size_t)4 * kMaxPassCh * kS * sizeof(float2) +
-                      (size_t)kMaxPassCh * kS * sizeof(float2) + (size_t)M.n * kS * sizeof(float2);
+                      (size_t)M.n * kS * sizeof(float2);
   dim3 grid((g.V3 + kS - 1) / kS, g.Nt);
   void* partial = nullptr;
   if (!sites) {
@@ -805,7 +878,7 @@ int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, c
   cudaError_t e = cudaSuccess;
 #define QDPG_ORBIT(T, SITES)                                                                                   \
   do {                                                                                                         \
-    auto k = meson_orbit_kernel<1, 1, kS, T, SITES>;                                                           \
+    auto k = same ? meson_orbit_kernel<1, 1, kS, T, SITES, true> : meson_orbit_kernel<1, 1, kS, T, SITES>;     \
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
     if (e == cudaSuccess)                                                                                      \
       k<<<grid, kS * 4, smem, s>>>(O, g, P, M, sites, S1->rec, S2->rec, site_scale,                            \
@@ -1246,8 +1319,7 @@ extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, cons
     pair_exp_kernel_t<<<(int)((n_rows + 127) / 128), 128, 0, s>>>(R, n_props, n_chan, static_cast<int*>(cexp));
     rc = check_launch("meson_2pt_multi scales");
   }
-  const size_t smem = (size_t)n_props * 144 * kS * esize + 16 + (size_t)4 * kOrbMaxProps * kMaxPassCh * kS * sizeof(float2) +
-                      (size_t)kMaxPassCh * kS * sizeof(float2) + (size_t)M.n * kS * sizeof(float2);
+  const size_t smem = (size_t)n_props * 144 * kS * esize + 16 + (size_t)4 * kOrbMaxProps * kMaxPassCh * kS * sizeof(float2);
   std::vector<int> mom_flat(moms, moms + 3 * (size_t)n_mom);
   for (int t0 = 0; t0 < g.Nt && rc == QDPG_OK; t0 += T) {
     const int nt = std::min(T, g.Nt - t0);
