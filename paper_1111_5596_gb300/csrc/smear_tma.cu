@@ -170,6 +170,24 @@ bool encode_psi_map(CUtensorMap* m, const void* in, const Geom& g, int esize, in
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// The same tensor with the row outermost, for row-major halo-tile stages:
+// dims (x; the 12 colour vectors of a spin row, stride V3; spin-row-colour +
+// 12*t, stride 12*V3; row = y + Ly*z, stride Lx), box (Lx, G vectors, 3
+// colours, `rows` rows), which lands in shared memory as [row][colour]
+// [vector][x].
+bool encode_psi_rm_map(CUtensorMap* m, const void* in, const Geom& g, int esize, int rows, int G) {
+  const EncodeTiledFn fn = encode_tiled();
+  if (!fn) return false;
+  const cuuint64_t Lx = g.sL[0], V3 = g.V3;
+  const cuuint64_t dims[4] = {Lx, 12, 12 * (cuuint64_t)g.Nt, (cuuint64_t)g.sL[1] * g.sL[2]};
+  const cuuint64_t strides[3] = {V3 * esize, 12 * V3 * esize, Lx * esize};
+  const cuuint32_t box[4] = {(cuuint32_t)Lx, (cuuint32_t)G, 3, (cuuint32_t)rows};
+  const cuuint32_t estr[4] = {1, 1, 1, 1};
+  return fn(m, esize == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4,
+            const_cast<void*>(in), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // The configuration a launch uses: explicit tuning settings first, then the
 // autotuning table, then the defaults.
 TileCfg current_cfg(const Geom& g, int psi_prec, int lprec) {
@@ -208,6 +226,15 @@ int launch_hop_tma_cfg(const tma_smear::JobPtrs* jobs, int njobs, int lprec, int
     if (reinterpret_cast<uintptr_t>(jobs[i].in) % 16 != 0 ||
         !encode_psi_map(&a.jobs.tmap[i], jobs[i].in, g, esize, a.tt.k, a.tt.G))
       a.tt.use_tmap = 0;
+  // halo tiles: row-major stages from five tensor-map copies (the fixed-shape
+  // kernels; a row of a stage must start on a 128-byte boundary)
+  a.tt.use_rm = !debug_tensor_copy_off() && a.tt.halo && a.tt.k <= 256 && g.sL[0] <= 256 &&
+                ((size_t)3 * a.tt.G * g.sL[0] * esize) % 128 == 0;
+  for (int i = 0; i < njobs && a.tt.use_rm; ++i)
+    if (reinterpret_cast<uintptr_t>(jobs[i].in) % 16 != 0 ||
+        !encode_psi_rm_map(&a.jobs.tmap[i], jobs[i].in, g, esize, a.tt.k, a.tt.G) ||
+        !encode_psi_rm_map(&a.jobs.tmap_row[i], jobs[i].in, g, esize, 1, a.tt.G))
+      a.tt.use_rm = 0;
   a.g = g;
   a.timeout_ns = wait_timeout_ns();
   a.drop_stage = debug_drop_vector();

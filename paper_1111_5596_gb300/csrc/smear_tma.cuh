@@ -29,7 +29,13 @@
 //    drains its own copies (bounded as well) before the CTA exits;
 //  * for the common tile shapes (LX > 0) the plane width, rows and halo are
 //    template constants, so every shared-memory operand is a register base
-//    plus an immediate offset.
+//    plus an immediate offset;
+//  * halo tiles of those shapes keep a stage row-major, element (row, colour
+//    q, vector gg, x) at ((row * 3 + q) * G + gg) * Lx + x, so that boxes of
+//    whole rows for all three colours and the stage's G vectors stack: a
+//    stage is five tensor-map copies (rows y0-1, y0..y0+k-1 and y0+k of
+//    plane z, the same k rows of planes z-1 and z+1) instead of one bulk
+//    copy per row run, colour and vector.
 #pragma once
 
 #include <cuda.h>  // CUtensorMap (the type only; maps are encoded through the runtime's driver entry point)
@@ -69,6 +75,7 @@ struct TmaTile {
   int grid;       // persistent CTAs
   int smem;       // dynamic shared memory bytes
   int use_tmap;   // 1: whole-plane tiles stage planes z-1..z+1 with one tensor-map copy
+  int use_rm;     // 1: halo tiles of a fixed shape stage row-major with tensor-map copies
 };
 
 // Jobs of one launch: same lattice and precisions, own fields and kappa.
@@ -82,11 +89,15 @@ struct JobPtrs {
 };
 // tmap[i]: job i's input propagator as a 4-D tensor (x; row = y + Ly*z;
 // the 12 colour vectors of a spin row; spin-row-colour + 12*t), for the
-// whole-plane tiles' tensor-map copies (TmaTile::use_tmap).
+// whole-plane tiles' tensor-map copies (TmaTile::use_tmap); for row-major
+// halo tiles (TmaTile::use_rm) the same tensor with the row outermost (x;
+// vector; spin-row-colour + 12*t; row), boxes of k rows, and tmap_row[i] its
+// one-row boxes.
 struct JobTable {
   int njobs;
   JobPtrs j[kMaxJobs];
   CUtensorMap tmap[kMaxJobs];
+  CUtensorMap tmap_row[kMaxJobs];
 };
 
 struct HopLaunch {
@@ -183,6 +194,11 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
   const int kLx = k * Lx;
   const int CS = rows * Lx;  // elements per colour region of a stage
   const int stage_elems = G * 3 * CS;
+  // stage strides (elements) of a row, a colour and a vector: region-major
+  // ([q][gg][row][x]) or, for halo tiles of a fixed shape, row-major
+  // ([row][q][gg][x])
+  constexpr bool RM = LX > 0 && HALO == 1;
+  const int RS = RM ? 3 * G * Lx : Lx, QS = RM ? G * Lx : G * CS, VS = RM ? Lx : CS;
   const uint32_t stage_bytes = (uint32_t)stage_elems * sizeof(PsiT);
   const int lel = link_elems(NE, k, Lx, halo);
   const uint32_t link_bytes = (uint32_t)lel * sizeof(LT);
@@ -284,6 +300,22 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
         if (gstage == drop_stage) continue;  // test hook: the waits for this stage run out
         if (lane == 0) ptx::mbar_arrive_expect_tx(full0 + 8 * s, stage_bytes);
         __syncwarp();
+        if constexpr (RM) {
+          // rows y0-1 (0), y0..y0+k-1 (1..k), y0+k (k+1) of plane z, then
+          // the k rows of planes z-1 and z+1: five boxes of all three colours
+          // and the stage's G vectors
+          if (lane < 5) {
+            const int v = p.part * VPI + j * G;
+            const int c1 = v % COLS, c2 = 3 * (v / COLS) + COLS * p.t;
+            const int dst_row = lane == 0 ? 0 : (lane == 1 ? 1 : (lane == 2 ? k + 1 : (lane == 3 ? k + 2 : 2 * k + 2)));
+            const int src_y = lane == 0 ? ym : (lane == 2 ? yp : p.y0);
+            const int src_z = lane == 3 ? zm : (lane == 4 ? zp : p.z);
+            const CUtensorMap* m = (lane == 0 || lane == 2) ? &J.tmap_row[job] : &J.tmap[job];
+            ptx::tensor_g2s_4d(ptx::smem_addr(st + (size_t)s * stage_elems + (size_t)dst_row * RS), m, 0, c1, c2,
+                               src_y + Ly * src_z, full0 + 8 * s);
+          }
+          continue;
+        }
         if (tt.use_tmap && npieces == 1) {
           // one box: x, rows of planes z-1..z+1, the stage's G vectors, 3 colours
           const int v = p.part * VPI + j * G;
@@ -358,11 +390,11 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
   // sites; rows of plane z from bz, of planes z-1 and z+1 from bzm and bzp
   const int bz = halo ? 0 : k, bzm = halo ? rowsA : 0, bzp = halo ? rowsA + k : 2 * k;
   const int rc = bz + r + halo;
-  const int oc = rc * Lx + x;
+  const int oc = rc * RS + x;
   const int yp_row = bz + (halo ? r + 2 : (r + 1 == k ? 0 : r + 1));
   const int ym_row = bz + (halo ? r : (r == 0 ? k - 1 : r - 1));
-  const int of[3] = {rc * Lx + (x + 1 == Lx ? 0 : x + 1), yp_row * Lx + x, (bzp + r) * Lx + x};
-  const int ob[3] = {rc * Lx + xm, ym_row * Lx + x, (bzm + r) * Lx + x};
+  const int of[3] = {rc * RS + (x + 1 == Lx ? 0 : x + 1), yp_row * RS + x, (bzp + r) * RS + x};
+  const int ob[3] = {rc * RS + xm, ym_row * RS + x, (bzm + r) * RS + x};
   // link-buffer offsets of this site's six links
   const int lf = r * Lx + x;
   const bool yh = halo && r == 0;
@@ -408,18 +440,18 @@ __global__ void __launch_bounds__(TileLaunch<LX, KR>::threads, TileLaunch<LX, KR
         PsiT* po = outp + (size_t)((v0 / COLS) * 3 * COLS + (v0 % COLS)) * V3;
 #pragma unroll
         for (int gg = 0; gg < G; ++gg) {
-          const PsiT* sg = sp + gg * CS;  // colour q of vector gg: region q * G + gg
+          const PsiT* sg = sp + gg * VS;  // colour q of vector gg
           u64 nf[3][3], nb[3][3];
           float2 c[3], o[3];
 #pragma unroll
           for (int i = 0; i < 3; ++i)
 #pragma unroll
             for (int q = 0; q < 3; ++q) {
-              nf[i][q] = lds_pair(sg + of[i] + q * G * CS);
-              nb[i][q] = lds_pair(sg + ob[i] + q * G * CS);
+              nf[i][q] = lds_pair(sg + of[i] + q * QS);
+              nb[i][q] = lds_pair(sg + ob[i] + q * QS);
             }
 #pragma unroll
-          for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * G * CS);
+          for (int a = 0; a < 3; ++a) c[a] = lds(sg + oc + a * QS);
           hop_vector(L, nf, nb, c, o);
 #pragma unroll
           for (int a = 0; a < 3; ++a) st2(po + (gg + a * COLS) * V3, o[a]);
@@ -479,8 +511,9 @@ template <typename PsiT, int LMODE>
 int launch_tma_any(const HopLaunch& a) {
   const int Lx = a.g.sL[0];
   constexpr int G = 2;
-#define QDPG_TMA_TRY(LXV, KV, HV) \
-  if (Lx == LXV && a.tt.k == KV && a.tt.halo == HV) return launch_tma_t<PsiT, LMODE, LXV, KV, HV, G>(a);
+#define QDPG_TMA_TRY(LXV, KV, HV)                                                 \
+  if (Lx == LXV && a.tt.k == KV && a.tt.halo == HV && (HV == 0 || a.tt.use_rm)) \
+    return launch_tma_t<PsiT, LMODE, LXV, KV, HV, G>(a);
   QDPG_TMA_FIXED_SHAPES(QDPG_TMA_TRY)
 #undef QDPG_TMA_TRY
   return launch_tma_t<PsiT, LMODE, 0, 0, 0, G>(a);

@@ -15,30 +15,38 @@ def _field(q, lat, kind, prec, canon):
     return q.Field(lat, kind, prec, device="cuda:0").import_(torch.from_numpy(canon.astype(np.complex64)).to("cuda:0"))
 
 
-@pytest.mark.parametrize("dims,prec,sites", [((16, 16, 16, 4), "f32", 0), ((8, 12, 6, 3), "f32", 0),
-                                             ((24, 24, 8, 2), "f32", 0), ((24, 24, 4, 2), "f32", 288),
-                                             ((48, 12, 3, 2), "bf16", 288), ((8, 8, 8, 4), "bf16", 0),
-                                             ((12, 6, 4, 2), "bf16", 0), ((16, 16, 2, 3), "f32", 0),
-                                             ((16, 8, 1, 2), "f32", 0), ((16, 16, 3, 2), "bf16", 0)])
-def test_pipelined_equals_simple_kernel(qdpg_gpu, dims, prec, sites):
+@pytest.mark.parametrize("dims,prec,sites,lprec", [
+    ((16, 16, 16, 4), "f32", 0, "f32"), ((8, 12, 6, 3), "f32", 0, "f32"),
+    ((24, 24, 8, 2), "f32", 0, "f32"), ((24, 24, 4, 2), "f32", 288, "f32"),
+    ((48, 12, 3, 2), "bf16", 288, "f32"), ((8, 8, 8, 4), "bf16", 0, "f32"),
+    ((12, 6, 4, 2), "bf16", 0, "f32"), ((16, 16, 2, 3), "f32", 0, "f32"),
+    ((16, 8, 1, 2), "f32", 0, "f32"), ((16, 16, 3, 2), "bf16", 0, "f32"),
+    # every fixed halo-tile shape (row-major stages from tensor-map copies)
+    ((16, 16, 4, 2), "f32", 128, "f32"), ((48, 12, 3, 2), "f32", 288, "f32"),
+    ((24, 16, 2, 2), "f32", 96, "f32"), ((48, 8, 3, 2), "f32", 96, "f32"),
+    ((24, 24, 3, 2), "f32", 192, "f32"), ((48, 12, 2, 2), "f32", 192, "f32"),
+    ((24, 24, 2, 2), "f32", 288, "f32_r12"), ((16, 16, 4, 2), "bf16", 128, "bf16_r12"),
+    ((48, 12, 3, 2), "bf16", 288, "bf16")])
+def test_pipelined_equals_simple_kernel(qdpg_gpu, dims, prec, sites, lprec):
     """sites: most sites per tile (0 = default); 288 gives 12-row tiles at
     Lx = 24 and 6-row tiles at Lx = 48.  Whole-plane tiles with Lz = 1, 2, 3
     cover the staging of planes z-1, z, z+1 in one, two or three copies;
-    halo tiles at the first, last and inner rows cover the y-halo runs."""
+    halo tiles at the first, last and inner rows cover the y-halo runs,
+    and every fixed halo shape (Lx 16, 24, 48) its row-major stages."""
     q = qdpg_gpu
     q.debug_set(q.TUNE_TILE_CONSUMERS, sites)
     try:
-        _pipelined_vs_simple(q, dims, prec)
+        _pipelined_vs_simple(q, dims, prec, lprec)
     finally:
         q.debug_set(q.TUNE_TILE_CONSUMERS, 0)
 
 
-def _pipelined_vs_simple(q, dims, prec):
+def _pipelined_vs_simple(q, dims, prec, lprec="f32"):
     lat = q.Lattice(dims, 3)
     U = fields.round_to_f32(fields.gauge_field(dims, 31, kind="haar"))
     psi = fields.round_to_f32(fields.propagator(dims, 31, envelope=0.3))
     p = q.PREC_NAMES[prec]
-    Uf = _field(q, lat, q.GAUGE, q.F32, U)
+    Uf = _field(q, lat, q.GAUGE, q.PREC_NAMES[lprec], U)
     a = _field(q, lat, q.PROPAGATOR, p, psi)
     b = _field(q, lat, q.PROPAGATOR, p, psi)
     q.gauss_smear(Uf, a, 0.2, 3, scratch=a.like())                # pipelined kernel
@@ -50,7 +58,7 @@ def _pipelined_vs_simple(q, dims, prec):
     q.device_status()
     ea, eb = a.export().cpu().numpy(), b.export().cpu().numpy()
     assert np.array_equal(ea, eb)
-    if prec == "f32":
+    if prec == "f32" and lprec == "f32":
         assert field_err(ea, smear.gauss_smear(U, psi, 0.2, 3)) <= TOL_F32
 
 
@@ -104,12 +112,14 @@ def test_autotuner_picks_a_config_and_keeps_parity(qdpg_gpu, tmp_path):
     assert f"16 16 8 2 3 {q.F32} {q.F32} {sites} {grid_mode}" in text
 
 
-@pytest.mark.parametrize("prec", ["f32", "bf16"])
-def test_tensor_map_and_bulk_staging_agree(qdpg_gpu, prec):
+@pytest.mark.parametrize("prec,dims,sites", [("f32", (16, 16, 6, 2), 0), ("bf16", (16, 16, 6, 2), 0),
+                                             ("f32", (24, 24, 4, 2), 288), ("f32", (48, 12, 3, 2), 96)])
+def test_tensor_map_and_bulk_staging_agree(qdpg_gpu, prec, dims, sites):
     """Whole-plane tiles stage interior planes with one tensor-map copy per
-    stage; the bulk-copy staging of the same rows gives the same bits."""
+    stage, halo tiles of a fixed shape stage row-major with five; the
+    bulk-copy staging of the same rows gives the same bits."""
     q = qdpg_gpu
-    dims = (16, 16, 6, 2)
+    q.debug_set(q.TUNE_TILE_CONSUMERS, sites)
     lat = q.Lattice(dims, 3)
     U = fields.round_to_f32(fields.gauge_field(dims, 37, kind="haar"))
     psi = fields.round_to_f32(fields.propagator(dims, 37, envelope=0.3))
@@ -125,6 +135,7 @@ def test_tensor_map_and_bulk_staging_agree(qdpg_gpu, prec):
             outs.append(f.export().cpu().numpy())
         finally:
             q.debug_set(q.TUNE_TENSOR_COPY, 0)
+    q.debug_set(q.TUNE_TILE_CONSUMERS, 0)
     assert np.array_equal(outs[0], outs[1])
     if prec == "f32":
         assert field_err(outs[0], smear.gauss_smear(U, psi, 0.2, 4)) <= TOL_F32
