@@ -128,8 +128,10 @@ __device__ __forceinline__ ItemPos decode(int it, const Tile& tt, int Lz) {
   return p;
 }
 
-// NE: stored entries per link; CW: consumer warps (each owns 64/CW sites of a tile).
-template <int NE, int CW>
+// NE: stored entries per link; CW: consumer warps; SPW: sites per consumer
+// warp (CW * SPW >= the tile's sites; sites beyond the tile are clamped
+// copies whose results are not stored).
+template <int NE, int CW, int SPW>
 __global__ void __launch_bounds__((CW + 1) * 32, 1)
     smear_hop_mma_kernel(const __grid_constant__ JobTable J, Geom g, Tile tt, int iter, unsigned int* status,
                          long long timeout_ns) {
@@ -149,7 +151,7 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
   const uint32_t lempty = ptx::smem_addr(bars + 2 * S + 1);
   const uint32_t xdone = ptx::smem_addr(bars + 2 * S + 2);  // reconstruct-12 expansion done
   constexpr int kConsumerWarps = CW;
-  constexpr int kSPW = kMaxTile / CW;  // sites per consumer warp
+  constexpr int kSPW = SPW;  // sites per consumer warp
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int total = tt.nitems * J.njobs;
 
@@ -519,9 +521,9 @@ bool pick_tile(const Geom& g, int ne, int njobs, Tile& tt) {
   return true;
 }
 
-template <int NE, int CW>
+template <int NE, int CW, int SPW>
 int launch_t(const JobTable& J, const Geom& g, const Tile& tt, int iter, cudaStream_t s) {
-  auto kern = smear_hop_mma_kernel<NE, CW>;
+  auto kern = smear_hop_mma_kernel<NE, CW, SPW>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, tt.smem);
   if (e != cudaSuccess) return fail(QDPG_ERR_CUDA, "gauss_smear (f16): smem attribute: %s", cudaGetErrorString(e));
   cudaLaunchConfig_t cfg = {};
@@ -565,8 +567,12 @@ int launch_hop_f16(const F16HopJob* jobs, int njobs, int lprec, const Geom& g, i
   for (int i = 0; i < njobs; ++i)
     J.j[i] = Job{static_cast<const uint32_t*>(jobs[i].in), static_cast<uint32_t*>(jobs[i].out),
                  static_cast<const uint32_t*>(jobs[i].U), jobs[i].kappa, jobs[i].rec};
-  if (debug_f16_warps() == 8) return ne == 6 ? launch_t<6, 8>(J, g, tt, iter, s) : launch_t<9, 8>(J, g, tt, iter, s);
-  return ne == 6 ? launch_t<6, 16>(J, g, tt, iter, s) : launch_t<9, 16>(J, g, tt, iter, s);
+  if (debug_f16_warps() == 8)
+    return ne == 6 ? launch_t<6, 8, 8>(J, g, tt, iter, s) : launch_t<9, 8, 8>(J, g, tt, iter, s);
+  // 48-site tiles (x extent 24 or 48): twelve consumer warps of four sites
+  // each, rather than sixteen of which a quarter compute clamped copies
+  if (tt.T == 48) return ne == 6 ? launch_t<6, 12, 4>(J, g, tt, iter, s) : launch_t<9, 12, 4>(J, g, tt, iter, s);
+  return ne == 6 ? launch_t<6, 16, 4>(J, g, tt, iter, s) : launch_t<9, 16, 4>(J, g, tt, iter, s);
 }
 
 int f16_scale_init(ScaleRecord* const* recs, const int* n_iter, int njobs, cudaStream_t s) {
