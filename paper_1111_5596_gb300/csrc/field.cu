@@ -3,6 +3,8 @@
 // Source creation is the first stage of the paper's Chroma measurement
 // (Sec. 5); shift is the nearest-neighbour primitive of QDP++ expressions
 // (Sec. 1).  All kernels here are pure data movement.
+#include <algorithm>
+#include <type_traits>
 #include <cuda_fp16.h>
 
 #include "qdpg_internal.h"
@@ -13,6 +15,7 @@ namespace qdpg {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kTileSites = 32;  // sites per tile of the propagator import (32 x 145 complex64 in shared memory)
 
 inline int grid_for(long long n) {
   long long b = (n + kThreads - 1) / kThreads;
@@ -34,6 +37,13 @@ __device__ __forceinline__ void store_elem(__nv_bfloat162* p, double re, double 
 __device__ __forceinline__ void store_elem(__half2* p, double re, double im) {
   *p = __halves2half2(__double2half(re), __double2half(im));
 }
+// From FP32 values: one rounding, the same as from the equal FP64 values,
+// without FP64 arithmetic (slow on this GPU).
+__device__ __forceinline__ void store_elem(float2* p, float re, float im) { *p = make_float2(re, im); }
+__device__ __forceinline__ void store_elem(__nv_bfloat162* p, float re, float im) {
+  *p = __floats2bfloat162_rn(re, im);
+}
+__device__ __forceinline__ void store_elem(__half2* p, float re, float im) { *p = __floats2half2_rn(re, im); }
 __device__ __forceinline__ void load_elem(const __half2* p, double& re, double& im) {
   const float2 v = __half22float2(*p);
   re = v.x;
@@ -211,8 +221,12 @@ template <typename Src>
 __global__ void __launch_bounds__(kThreads) f16_max_kernel(const Src* __restrict__ src, long long n,
                                                            unsigned* __restrict__ out) {
   float m = 0.f;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    m = fmaxf(m, __double2float_ru(fmax(fabs((double)src[i]), 0.0)));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    if constexpr (std::is_same<Src, float>::value)
+      m = fmaxf(m, fabsf(src[i]));  // exact
+    else
+      m = fmaxf(m, __double2float_ru(fmax(fabs((double)src[i]), 0.0)));  // rounded up: still a bound
+  }
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(out, __float_as_uint(m));
@@ -235,6 +249,69 @@ __global__ void __launch_bounds__(kThreads) f16_import_kernel(__half2* __restric
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     rec->exp = e;
     rec->maxabs = ldexpf(m, -e) * (1.f + 1.f / 1024.f);  // bound after rounding to float16
+  }
+}
+
+// Propagators and fermions (NC = 144 or 12 complex entries per site), by
+// tiles of TS consecutive device sites of one timeslice: a block reads the
+// tile's canonical entries (each site's NC numbers are contiguous) with
+// coalesced loads into shared memory, rows padded by one entry so that
+// column reads spread over the banks, and writes them in the device layout
+// with coalesced stores: component planes for F32/BF16, site-major vector
+// groups scaled by 2^-e for float16 (F16: e from the whole field's maximum,
+// as f16_import_kernel).
+template <typename Src, typename Dst, int NC, int TS, bool F16>
+__global__ void __launch_bounds__(kThreads) import_tile_kernel(Dst* __restrict__ dst, const Src* __restrict__ src,
+                                                               Geom g, Chunk ck, ScaleRecord* rec) {
+  __shared__ Src sm[TS][NC + 1][2];
+  __shared__ long long sbase[TS];
+  const int ntile = (g.V3 + TS - 1) / TS;
+  const long long ntot = (long long)ck.nt * ntile;
+  int e = 0;
+  float m = 0.f;
+  if constexpr (F16) {
+    m = __uint_as_float(rec->tmpmax);
+    e = f16_exp_for(m);
+  }
+  for (long long tile = blockIdx.x; tile < ntot; tile += gridDim.x) {
+    const int t = ck.t0 + (int)(tile / ntile);
+    const int s0 = (int)(tile % ntile) * TS;
+    const int ns = min(TS, g.V3 - s0);
+    if (threadIdx.x < ns) sbase[threadIdx.x] = (canon_site(g, t, s0 + threadIdx.x) - ck.site0) * NC;
+    __syncthreads();
+    for (int i = threadIdx.x; i < ns * NC; i += kThreads) {
+      const int si = i / NC, c = i - si * NC;
+      const long long ci = sbase[si] + c;
+      sm[si][c][0] = src[2 * ci];
+      sm[si][c][1] = src[2 * ci + 1];
+    }
+    __syncthreads();
+    if constexpr (!F16) {
+      for (int i = threadIdx.x; i < NC * TS; i += kThreads) {
+        const int c = i / TS, si = i - c * TS;
+        if (si < ns) store_elem(dst + ((long long)t * NC + c) * g.V3 + s0 + si, sm[si][c][0], sm[si][c][1]);
+      }
+    } else {
+      // word ((t*3 + vg)*V3 + s3)*48 + w, w = (v mod 16)*3 + colour (qdpg.h)
+      for (int i = threadIdx.x; i < 3 * TS * 48; i += kThreads) {
+        const int vg = i / (TS * 48), r = i - vg * (TS * 48), si = r / 48, w = r - si * 48;
+        if (si >= ns) continue;
+        const int v = vg * 16 + w / 3, cc = w % 3;
+        const int comp = ((v / 12) * 3 + cc) * 12 + v % 12;
+        Dst* o = dst + (((long long)t * 3 + vg) * g.V3 + s0 + si) * 48 + w;
+        if constexpr (std::is_same<Src, float>::value)
+          store_elem(o, ldexpf(sm[si][comp][0], -e), ldexpf(sm[si][comp][1], -e));  // exact scaling, one rounding
+        else
+          store_elem(o, ldexp(sm[si][comp][0], -e), ldexp(sm[si][comp][1], -e));
+      }
+    }
+    __syncthreads();
+  }
+  if constexpr (F16) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      rec->exp = e;
+      rec->maxabs = ldexpf(m, -e) * (1.f + 1.f / 1024.f);  // bound after rounding to float16
+    }
   }
 }
 
@@ -329,11 +406,43 @@ int import_chunk(qdpg_field_t dst, const void* canon_dev, int canon, const Chunk
       else
         f16_max_kernel<<<grid_for(nreal), kThreads, 0, s>>>(static_cast<const float*>(canon_dev), nreal,
                                                             &dst->rec->tmpmax);
-    } else if (f64) {
-      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, dst->rec, ck);
     } else {
-      f16_import_kernel<<<grid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, dst->rec, ck);
+      const long long tiles = (long long)ck.nt * ((dst->g.V3 + kTileSites - 1) / kTileSites);
+      const int tgrid = (int)std::min<long long>(tiles, 152LL * 8);
+      if (f64)
+        import_tile_kernel<double, __half2, 144, kTileSites / 2, true>
+            <<<tgrid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, ck, dst->rec);
+      else
+        import_tile_kernel<float, __half2, 144, kTileSites, true>
+            <<<tgrid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, ck, dst->rec);
     }
+    return check_launch("field_import");
+  }
+  if (dst->kind == QDPG_PROPAGATOR || dst->kind == QDPG_FERMION) {
+    // tiles of consecutive sites through shared memory (16 sites for FP64
+    // canonical data, whose rows are twice as long)
+    const int TSf = dst->kind == QDPG_PROPAGATOR ? kTileSites : 4 * kTileSites;
+    const long long tiles = (long long)ck.nt * ((dst->g.V3 + TSf - 1) / TSf);
+    const int tgrid = (int)std::min<long long>(f64 ? 2 * tiles : tiles, 152LL * 8);
+#define QDPG_TILE(DT, NC, TS)                                                                                    \
+  do {                                                                                                           \
+    auto* d = static_cast<DT*>(dst->data);                                                                       \
+    if (f64)                                                                                                     \
+      import_tile_kernel<double, DT, NC, (TS) / 2, false>                                                        \
+          <<<tgrid, kThreads, 0, s>>>(d, static_cast<const double*>(canon_dev), dst->g, ck, nullptr);           \
+    else                                                                                                         \
+      import_tile_kernel<float, DT, NC, TS, false>                                                               \
+          <<<tgrid, kThreads, 0, s>>>(d, static_cast<const float*>(canon_dev), dst->g, ck, nullptr);            \
+  } while (0)
+    const bool prop = dst->kind == QDPG_PROPAGATOR;
+    if (is_bf16(dst->prec)) {
+      if (prop) QDPG_TILE(__nv_bfloat162, 144, kTileSites);
+      else QDPG_TILE(__nv_bfloat162, 12, 4 * kTileSites);
+    } else {
+      if (prop) QDPG_TILE(float2, 144, kTileSites);
+      else QDPG_TILE(float2, 12, 4 * kTileSites);
+    }
+#undef QDPG_TILE
     return check_launch("field_import");
   }
 #define QDPG_IMPORT(DT)                                                                                          \

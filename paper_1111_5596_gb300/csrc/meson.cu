@@ -780,12 +780,14 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
       }
     } else {
       // timeslice/momentum sums of the block's sites (NA = NB = 1): thread
-      // (channel tid / 8, sites 4 (tid % 8) .. +3) adds the four orbits'
-      // parts of its sites, multiplies them by the phases and sums them in
-      // two-float arithmetic; the channel's eight lanes finish each sum
-      // with a three-step butterfly
-      static_assert(SITES || (OK_S == 32 && NA == 1), "the reducing form takes one pair and 32 sites per block");
-      const int uj = tid >> 3, g4 = (tid & 7) * 4;
+      // (channel tid / TPC, sites 4 (tid % TPC) .. +3) adds the four
+      // orbits' parts of its sites, multiplies them by the phases and sums
+      // them in two-float arithmetic; the channel's TPC = OK_S / 4 lanes
+      // finish each sum with a butterfly
+      constexpr int TPC = OK_S / 4;
+      static_assert(SITES || (NA == 1 && OK_S % 4 == 0 && TPC <= 32 && (TPC & (TPC - 1)) == 0),
+                    "the reducing form takes one pair and 4 sites per lane, a power-of-two lanes per channel");
+      const int uj = tid / TPC, g4 = (tid % TPC) * 4;
       const int nv = P.nch * M.n;
       float2 cs[4];
 #pragma unroll
@@ -815,7 +817,7 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
           lo.y += ey;
         }
 #pragma unroll
-        for (int o = 4; o > 0; o >>= 1) {
+        for (int o = TPC / 2; o > 0; o >>= 1) {
           const float hx = __shfl_xor_sync(0xffffffffu, hi.x, o), lx = __shfl_xor_sync(0xffffffffu, lo.x, o);
           const float hy = __shfl_xor_sync(0xffffffffu, hi.y, o), ly = __shfl_xor_sync(0xffffffffu, lo.y, o);
           float ex, ey;
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
           lo.x = lo.x + lx + ex;
           lo.y = lo.y + ly + ey;
         }
-        if ((tid & 7) == 0 && uj < P.nch)
+        if (tid % TPC == 0 && uj < P.nch)
           partial[((long long)t * gridDim.x + blockIdx.x) * nv + uj * M.n + m] =
               make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
       }
@@ -838,9 +840,14 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
 // where it does not apply (a channel with different masks, float16's
 // site-major layout, a component row not a multiple of 16 bytes, no
 // tensor-map support).
+// Sites per block, for site-value output and for the reducing form (32 each:
+// measured faster than 16-site blocks at 16^3x32 and 24^3x48).
+constexpr int kOrbitSitesS = 32;
+constexpr int kOrbitSitesR = 32;
+
 int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
                       float2* sites, cudaStream_t s, int site_scale) {
-  constexpr int kS = 32;
+  const int kS = sites ? kOrbitSitesS : kOrbitSitesR;
   const Geom& g = S1->g;
   const bool bf = S1->prec == QDPG_BF16;
   if (S1->prec != QDPG_F32 && !bf) return QDPG_ERR_UNSUPPORTED;
@@ -878,7 +885,8 @@ int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, c
   cudaError_t e = cudaSuccess;
 #define QDPG_ORBIT(T, SITES)                                                                                   \
   do {                                                                                                         \
-    auto k = same ? meson_orbit_kernel<1, 1, kS, T, SITES, true> : meson_orbit_kernel<1, 1, kS, T, SITES>;     \
+    constexpr int KS = SITES ? kOrbitSitesS : kOrbitSitesR;                                                    \
+    auto k = same ? meson_orbit_kernel<1, 1, KS, T, SITES, true> : meson_orbit_kernel<1, 1, KS, T, SITES>;     \
     e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
     if (e == cudaSuccess)                                                                                      \
       k<<<grid, kS * 4, smem, s>>>(O, g, P, M, sites, S1->rec, S2->rec, site_scale,                            \
