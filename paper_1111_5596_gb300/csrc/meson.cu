@@ -576,11 +576,15 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
   // F32/BF16: [prop][144 comps][OK_S sites]; float16 (site-major fields):
   // [prop][3 vector groups][OK_S sites][48 words]
   constexpr bool kF16 = std::is_same<PsiT, __half2>::value;
+  // a float16 self pair is converted once into FP32 rows of one site's 144
+  // components (padded to 145: a warp's column reads hit distinct banks)
+  constexpr bool kF16T = kF16 && SAME && NA == 1;
   PsiT* st = reinterpret_cast<PsiT*>(smem_raw);
   constexpr uint32_t kPropBytes = 144u * OK_S * sizeof(PsiT);
   uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)O.np * kPropBytes);
   float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][kMaxPassCh][NA][OK_S] orbit parts
-  float2* phase = cpart + 4 * NA * kMaxPassCh * OK_S;     // [n_mom][OK_S] (reducing form)
+  float2* tr = cpart + 4 * NA * kMaxPassCh * OK_S;        // [OK_S][145] (float16 self pair)
+  float2* phase = tr + (kF16T ? OK_S * 145 : 0);          // [n_mom][OK_S] (reducing form)
   const int tid = threadIdx.x;
   // warp-uniform orbit: thread = ((d * NA) + ia) * OK_S + site
   const int site = tid % OK_S, ia = (tid / OK_S) % NA, d = tid / (OK_S * NA);
@@ -612,9 +616,23 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
     }
     return;
   }
+  if constexpr (kF16T) {
+    // [3 vector groups][OK_S sites][48 words] -> [site][component], FP32;
+    // word w of group vg is vector v = 16 vg + w / 3, sink colour w % 3
+    const uint32_t* L = reinterpret_cast<const uint32_t*>(smem_raw);
+    for (int idx = tid; idx < 3 * OK_S * 48; idx += kThreads) {
+      const int vg = idx / (OK_S * 48), r = idx - vg * (OK_S * 48), ss = r / 48, w = r - ss * 48;
+      const int v = vg * 16 + w / 3, c = w % 3;
+      tr[ss * 145 + ((v / 12) * 3 + c) * 12 + v % 12] = f16_word(L[idx]);
+    }
+    __syncthreads();
+  }
   // element (comp) of staged propagator i at this thread's site
   auto elem = [&](int i, int comp) -> u64 {
-    if constexpr (kF16) {
+    if constexpr (kF16T) {
+      (void)i;
+      return lds_pair_st(tr + site * 145 + comp);
+    } else if constexpr (kF16) {
       const int w = f16_site_word(comp);  // vector group * 48 + word
       return lds_pair_st(st + (size_t)i * 144 * OK_S + ((w / 48) * OK_S + site) * 48 + w % 48);
     } else {
@@ -837,8 +855,8 @@ __global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid
 
 
 // The orbit kernel for one pass of one pair (S1, S2), or QDPG_ERR_UNSUPPORTED
-// where it does not apply (a channel with different masks, float16's
-// site-major layout, a component row not a multiple of 16 bytes, no
+// where it does not apply (a channel with different masks, two different
+// float16 propagators, a component row not a multiple of 16 bytes, no
 // tensor-map support).
 // Sites per block, for site-value output and for the reducing form (32 each:
 // measured faster than 16-site blocks at 16^3x32 and 24^3x48).
@@ -850,12 +868,13 @@ int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, c
   const int kS = sites ? kOrbitSitesS : kOrbitSitesR;
   const Geom& g = S1->g;
   const bool bf = S1->prec == QDPG_BF16;
-  if (S1->prec != QDPG_F32 && !bf) return QDPG_ERR_UNSUPPORTED;
+  const bool h16 = S1->prec == QDPG_F16;
+  const bool same = S1->data == S2->data;
+  if (S1->prec != QDPG_F32 && !bf && !(h16 && same)) return QDPG_ERR_UNSUPPORTED;  // float16: self pairs
   for (int q = 0; q < P.nq; ++q)
     if (P.ma[q] != P.mb[q]) return QDPG_ERR_UNSUPPORTED;
-  const int esize = bf ? 4 : 8;
-  if (((long long)g.V3 * esize) % 16 != 0) return QDPG_ERR_UNSUPPORTED;
-  const bool same = S1->data == S2->data;
+  const int esize = (bf || h16) ? 4 : 8;
+  if (!h16 && ((long long)g.V3 * esize) % 16 != 0) return QDPG_ERR_UNSUPPORTED;
   OrbitSet O{};
   O.np = same ? 1 : 2;
   O.na = O.nb = 1;
@@ -865,15 +884,19 @@ int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, c
   O.t0 = 0;
   O.nt_out = g.Nt;
   const qdpg_field* staged[2] = {S1, S2};
+  // F32/BF16: (site; component row) boxes of kS x 144; float16: (word; site;
+  // timeslice-vector-group) boxes of 48 x kS x 3
   for (int i = 0; i < O.np; ++i)
     if (reinterpret_cast<uintptr_t>(staged[i]->data) % 16 != 0 ||
-        !encode_map_2d(&O.map[i], staged[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
-                       (uint64_t)g.V3 * esize, kS, 144))
+        !(h16 ? encode_map_3d(&O.map[i], staged[i]->data, 4, 48, (uint64_t)g.V3, (uint64_t)g.Nt * 3, 48 * 4,
+                              (uint64_t)g.V3 * 48 * 4, 48, kS, 3)
+              : encode_map_2d(&O.map[i], staged[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
+                              (uint64_t)g.V3 * esize, kS, 144)))
       return QDPG_ERR_UNSUPPORTED;
   unsigned int* status = device_status_word();
   if (!status) return QDPG_ERR_UNSUPPORTED;
   const size_t smem = (size_t)O.np * 144 * kS * esize + 16 + (size_t)4 * kMaxPassCh * kS * sizeof(float2) +
-                      (size_t)M.n * kS * sizeof(float2);
+                      (h16 ? (size_t)kS * 145 * sizeof(float2) : 0) + (size_t)M.n * kS * sizeof(float2);
   dim3 grid((g.V3 + kS - 1) / kS, g.Nt);
   void* partial = nullptr;
   if (!sites) {
@@ -892,7 +915,10 @@ int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, c
       k<<<grid, kS * 4, smem, s>>>(O, g, P, M, sites, S1->rec, S2->rec, site_scale,                            \
                                    static_cast<double2*>(partial), status, wait_timeout_ns());                  \
   } while (0)
-  if (bf) {
+  if (h16) {
+    if (sites) QDPG_ORBIT(__half2, true);
+    else QDPG_ORBIT(__half2, false);
+  } else if (bf) {
     if (sites) QDPG_ORBIT(__nv_bfloat162, true);
     else QDPG_ORBIT(__nv_bfloat162, false);
   } else {

@@ -12,7 +12,7 @@ import torch
 
 from oracle import geometry, hadron, smear, source
 from synth import fields
-from tests.parity_util import TOL_BF16, corr_err, field_err, field_err_t
+from tests.parity_util import TOL_BF16, corr_err, field_err, field_err_t, proj_err
 
 pytestmark = pytest.mark.gpu
 
@@ -204,3 +204,36 @@ def test_f16_rejects_unserved_lattice(qdpg_gpu):
     with pytest.raises(q.QdpgError) as ei:
         q.gauss_smear(Uf, S, 0.2, 2, 3, scratch=S.like())
     assert ei.value.status == -7
+
+
+@pytest.mark.parametrize("dims,moms", [((8, 8, 8, 4), ((0, 0, 0),)), ((12, 6, 5, 2), ((0, 0, 0), (1, 0, 0))),
+                                       ((8, 8, 4, 2), "eight")])
+def test_f16_self_pair_orbit_form_agrees_with_global_reads(qdpg_gpu, dims, moms):
+    """A float16 self pair runs the orbit kernel (the staged float16 site
+    blocks converted once into FP32 rows per site); the global-read form
+    reads the same stored numbers: the two agree to FP32 rounding, with the
+    reducing sums (p = 0, two momenta) and with site values for the
+    projection (eight momenta), including a ragged last block (V3 = 360)."""
+    q = qdpg_gpu
+    lat = q.Lattice(dims, 3)
+    P = fields.round_to_f32(fields.propagator(dims, 44, envelope=0.4))
+    S = q.Field(lat, q.PROPAGATOR, q.F16, device=dev()).import_(upload(P.astype(np.complex64)))
+    mlist = q.momenta_up_to(2)[:8] if moms == "eight" else list(moms)
+    outs = []
+    for form in (0, 2):
+        q.debug_set(q.DEBUG_MESON_FORM, form)
+        try:
+            outs.append(q.meson_2pt(S, S, q.SIXTEEN_MESONS, moms=mlist).cpu().numpy())
+            q.device_status()
+        finally:
+            q.debug_set(q.DEBUG_MESON_FORM, 0)
+    Sx = export(S)
+    ref = hadron.meson_2pt(Sx, Sx, hadron.SIXTEEN_MESONS, moms=mlist)
+    # per channel, the sum over each timeslice of the site values' magnitudes
+    # (the scale a cancelling p != 0 sum is accurate to in FP32)
+    A = np.stack([np.abs(hadron.meson_site(Sx, Sx, a, b)).sum(axis=(1, 2, 3)) for a, b in hadron.SIXTEEN_MESONS])
+    for C in outs:
+        assert proj_err(C, ref, A[:, None, :]) <= 1e-5
+    k0 = [i for i, m in enumerate(mlist) if tuple(m) == (0, 0, 0)]
+    if k0:
+        assert corr_err(outs[0][:, k0[0], :], ref[:, k0[0], :]) <= 1e-5
