@@ -192,7 +192,10 @@ int qdpg_device_status(void* stream);
  *  QDPG_TUNE_F16_WARPS         consumer warps per CTA, 8 or 16 (0 = default, 16);
  *  QDPG_TUNE_TENSOR_COPY       FP32/BF16 pipelined hop: 0 (default) stages whole-plane
  *                              tiles with one tensor-map (TMA) copy per stage where
- *                              planes z-1..z+1 are consecutive, 1 uses bulk copies only. */
+ *                              planes z-1..z+1 are consecutive, and halo tiles of the
+ *                              fixed shapes (x extent 16, 24, 48) row-major with five
+ *                              tensor-map copies per stage; 1 uses bulk copies only
+ *                              (the same results bit for bit). */
 enum {
   QDPG_DEBUG_WAIT_TIMEOUT_NS = 1,
   QDPG_DEBUG_DROP_STAGE = 2,
