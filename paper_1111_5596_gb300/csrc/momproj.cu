@@ -346,16 +346,37 @@ int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* 
   for (int m = 0; m < n_mom; ++m)
     for (int k = 0; k < 3; ++k) P.k[m][k] = moms[3 * m + k];
   const int row_tiles = (int)((rows + kM - 1) / kM);
-  // split the sites so that about one wave of CTAs (two per SM) runs, each
-  // with at most kMaxCtaSites sites: the tensor-core accumulator is FP32, and
-  // its depth bounds the rounding error; longer sums add up in the FP64 fold
-  const int nchunk_all = (g.V3 + kChunk - 1) / kChunk;
-  int nsplit = std::max(1, std::min(nchunk_all, (2 * 152 + row_tiles - 1) / row_tiles));
-  nsplit = std::max(nsplit, (g.V3 + kMaxCtaSites - 1) / kMaxCtaSites);
-  P.sites_per_cta = (nchunk_all + nsplit - 1) / nsplit * kChunk;
-  nsplit = (g.V3 + P.sites_per_cta - 1) / P.sites_per_cta;
   const size_t stage_bytes = (size_t)2 * kM * kKt * 4 + (size_t)2 * P.npad * kKt * 4;
   const size_t smem = 2 * stage_bytes + 4 * sizeof(uint64_t) + 16;
+  // split the sites among CTAs of at most kMaxCtaSites sites each (the
+  // tensor-core accumulator is FP32 and its depth bounds the rounding error;
+  // longer sums add up in the FP64 fold), choosing the number of full waves
+  // of resident CTAs and the split that fills them with the fewest chunks
+  // per CTA: a grid a little over one wave would run its remainder as a
+  // second wave of full-length CTAs
+  const int nchunk_all = (g.V3 + kChunk - 1) / kChunk;
+  int dev = 0, nsm = 0, per_sm = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      cudaFuncSetAttribute(momproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, momproj_kernel, 128, smem) != cudaSuccess)
+    return fail(QDPG_ERR_CUDA, "momentum_project: device query failed");
+  const long long slots = std::max(1LL, (long long)nsm * std::max(1, per_sm));
+  const int min_split = (g.V3 + kMaxCtaSites - 1) / kMaxCtaSites;
+  int nsplit = std::max(1, min_split), best_cost = -1;
+  for (int w = 1; w <= 64; ++w) {
+    const int ns = (int)std::min<long long>(nchunk_all, slots * w / row_tiles);
+    if (ns < min_split) continue;
+    const int spc = (nchunk_all + ns - 1) / ns;                                   // chunks per CTA
+    const int waves = (int)(((long long)row_tiles * ((nchunk_all + spc - 1) / spc) + slots - 1) / slots);
+    const int cost = waves * (spc + 2);                                           // + pipeline fill per CTA
+    if (best_cost < 0 || cost < best_cost) {
+      best_cost = cost;
+      nsplit = ns;
+    }
+    if (ns == nchunk_all) break;
+  }
+  P.sites_per_cta = (nchunk_all + nsplit - 1) / nsplit * kChunk;
+  nsplit = (g.V3 + P.sites_per_cta - 1) / P.sites_per_cta;
   const int nchunk_pad = (g.V3 + kChunk - 1) / kChunk;
   const size_t tile_bytes = (size_t)nchunk_pad * 2 * P.npad * kKt * 4;
 
@@ -366,12 +387,6 @@ int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* 
   if (rc != QDPG_OK) {
     dev_free(partial, s);
     return rc;
-  }
-  cudaError_t e = cudaFuncSetAttribute(momproj_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) {
-    dev_free(partial, s);
-    dev_free(tiles, s);
-    return fail(QDPG_ERR_CUDA, "momentum_project: smem attribute: %s", cudaGetErrorString(e));
   }
   {
     ProfScope prof("momentum_project", s);
