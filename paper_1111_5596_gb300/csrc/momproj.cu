@@ -289,22 +289,38 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
 // partial sums: one thread per output, consecutive threads on consecutive
 // rows (coalesced reads of partial[split][col][row] and writes of out), the
 // splits added in order in two-float arithmetic (hi + lo), FP64 once.
+// Block (32 rows, momentum m): eight groups of 32 threads each add every
+// eighth CTA's partial sums of their row in two-float arithmetic (a warp
+// reads 32 consecutive rows of one partial), then the eight group sums of a
+// row are added in group order.
 __global__ void __launch_bounds__(256) momproj_fold_kernel(const float* __restrict__ partial, int nsplit, int rows,
                                                            int npad, int nmom, int Nt, double* __restrict__ out,
                                                            const ScaleRecord* ra, int ca, const ScaleRecord* rb,
                                                            int cb, const int* __restrict__ chan_exp) {
-  const long long total = (long long)rows * nmom;
-  const long long i = blockIdx.x * 256LL + threadIdx.x;
-  if (i >= total) return;
-  const int row = (int)(i % rows), m = (int)(i / rows);
+  __shared__ float4 acc[8][32];  // (hr, lr, hi, li) per group and row
+  const int rl = threadIdx.x & 31, grp = threadIdx.x >> 5;
+  const int row = blockIdx.x * 32 + rl, m = blockIdx.y;
   float hr = 0.f, lr = 0.f, hi = 0.f, li = 0.f;
-  for (int sp = 0; sp < nsplit; ++sp) {
-    const float* p = partial + (size_t)sp * npad * rows;
+  if (row < rows) {
+    for (int sp = grp; sp < nsplit; sp += 8) {
+      const float* p = partial + (size_t)sp * npad * rows;
+      float e;
+      two_sum(hr, p[(size_t)(2 * m) * rows + row], hr, e);
+      lr += e;
+      two_sum(hi, p[(size_t)(2 * m + 1) * rows + row], hi, e);
+      li += e;
+    }
+  }
+  acc[grp][rl] = make_float4(hr, lr, hi, li);
+  __syncthreads();
+  if (grp != 0 || row >= rows) return;
+  for (int g = 1; g < 8; ++g) {
+    const float4 v = acc[g][rl];
     float e;
-    two_sum(hr, p[(size_t)(2 * m) * rows + row], hr, e);
-    lr += e;
-    two_sum(hi, p[(size_t)(2 * m + 1) * rows + row], hi, e);
-    li += e;
+    two_sum(hr, v.x, hr, e);
+    lr += e + v.y;
+    two_sum(hi, v.z, hi, e);
+    li += e + v.w;
   }
   const int chan = row / Nt, t = row % Nt;
   const int ex = chan_exp ? chan_exp[chan] : (ra ? ca * ra->exp : 0) + (rb ? cb * rb->exp : 0);
@@ -402,8 +418,7 @@ int launch_momproj(const Geom& g, const void* sites_dev, int n_chan, const int* 
       rc = check_launch("momentum_project");
     }
     if (rc == QDPG_OK) {
-      const long long nout = rows * n_mom;
-      momproj_fold_kernel<<<(int)((nout + 255) / 256), 256, 0, s>>>(static_cast<const float*>(partial), nsplit,
+      momproj_fold_kernel<<<dim3((unsigned)((rows + 31) / 32), (unsigned)n_mom), 256, 0, s>>>(static_cast<const float*>(partial), nsplit,
                                                                   (int)rows, P.npad, n_mom, g.Nt, out_dev, ra, ca,
                                                                   rb, cb, chan_exp);
       rc = check_launch("momentum_project fold");
