@@ -18,9 +18,11 @@
 // Gamma_snk = Gamma_src = Gamma(n) use only four mask pairs: 64 colour
 // contractions (576 complex MACs) per site for all sixteen.
 //
-// A thread owns one site.  Site values are FP32; the timeslice/momentum sums
-// are FP64: warp shuffle, then shared memory across warps, then one FP64
-// atomic per block and value.
+// This file: the channel plan, the entry points, the staged form and the
+// fold of the blocks' partial sums; the orbit form is in meson_orbit.cu and
+// the global-read form in meson_global_*.cu (shared definitions in
+// meson_dev.cuh).  Site values are FP32; a block's timeslice/momentum sums
+// are two-float, folded over the blocks in FP64 in a fixed order.
 #include <cuda_fp16.h>
 
 #include <algorithm>
@@ -33,281 +35,12 @@
 #include "qdpg_internal.h"
 #include "qdpg_profile.h"
 #include "tmap.h"
-
+#include "meson_dev.cuh"
 namespace qdpg {
 
-namespace {
+namespace meson {
 
 using namespace gamma_host;
-
-constexpr int kMesonThreads = 128;
-constexpr int kMaxPassCh = 16;
-constexpr int kMaxMom = 64;
-
-struct MesonPass {
-  int nq;                        // distinct (ma, mb) pairs, 1..4
-  int ma[4], mb[4];
-  int nch;                       // channels, 1..16
-  int q_of[kMaxPassCh];          // pair index of each channel
-  int out_row[kMaxPassCh];       // channel index in the output
-  float2 w[kMaxPassCh][16];      // weight of Q_q[alpha*4 + beta]
-  int jlo[4], jhi[4];            // channels of pair q: jlo[q] <= j < jhi[q] (grouped by pair)
-  int mlo[4], mhi[4];            // channels whose two masks are both m (orbit kernel): mlo[m] <= j < mhi[m]
-  unsigned long long wre[kMaxPassCh][16];  // (w.x, w.x) and (w.y, w.y) as packed FP32 pairs
-  unsigned long long wim[kMaxPassCh][16];
-};
-
-struct Moms {
-  int n;
-  int origin[3];                 // origin along the three non-decay directions
-  int k[kMaxMom][3];             // integer momenta
-  bool zero_only;                // single momentum (0,0,0): no phases
-};
-
-__device__ __forceinline__ float2 ld2(const float2* p) { return __ldg(p); }
-typedef unsigned long long u64;
-__device__ __forceinline__ u64 pack2(float x, float y) {
-  u64 r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(x), "f"(y));
-  return r;
-}
-__device__ __forceinline__ float2 unpack2(u64 r) {
-  float2 v;
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(v.x), "=f"(v.y) : "l"(r));
-  return v;
-}
-// d = a (.) b + c, two FP32 lanes, round to nearest
-__device__ __forceinline__ u64 fma2(u64 a, u64 b, u64 c) {
-  u64 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-__device__ __forceinline__ u64 lds_pair_st(const float2* p) { return *reinterpret_cast<const u64*>(p); }
-__device__ __forceinline__ u64 lds_pair_st(const __nv_bfloat162* p) {
-  const float2 v = __bfloat1622float2(*p);
-  return pack2(v.x, v.y);
-}
-__device__ __forceinline__ u64 lds_pair_st(const __half2* p) {
-  const float2 v = __half22float2(*p);
-  return pack2(v.x, v.y);
-}
-__device__ __forceinline__ float2 lds_elem(const float2* p) { return *p; }
-__device__ __forceinline__ float2 lds_elem(const __nv_bfloat162* p) { return __bfloat1622float2(*p); }
-__device__ __forceinline__ float2 ld2(const __nv_bfloat162* p) {
-  __nv_bfloat162 v = *p;
-  return __bfloat1622float2(v);
-}
-
-// Element loaders of one site's propagator: component-major (F32, BF16)
-// and site-major float16 (qdpg.h); comp folds to a constant when unrolled.
-template <typename PsiT>
-struct SoASite {
-  const PsiT* p;
-  int V3;
-  __device__ SoASite(const PsiT* S, int t, int s3, int V3_) : p(S + (long long)t * 144 * V3_ + s3), V3(V3_) {}
-  __device__ __forceinline__ float2 operator()(int comp) const { return ld2(p + (long long)comp * V3); }
-};
-// Float16 propagators are site-major, so a thread's own site is 576 strided
-// bytes: the block's sites are first staged in shared memory with coalesced
-// 16-byte loads, kF16Stride words per site (odd: conflict-free reads).
-constexpr int kF16Stride = 145;
-// Loaders of one site's float16 propagator: staged in shared memory (the
-// site's 145-word slot, vector groups 48 words apart) or in global memory.
-__device__ __forceinline__ float2 f16_word(uint32_t w) { return __half22float2(*reinterpret_cast<const __half2*>(&w)); }
-__device__ __forceinline__ int f16_site_word(int comp) {  // vector group * 48 + word within the group
-  const int sc = comp / 12, sp = comp % 12, sv = sc / 3, c = sc % 3;
-  const int v = sv * 12 + sp;
-  return (v >> 4) * 48 + (v & 15) * 3 + c;
-}
-struct F16Staged {
-  const uint32_t* p;
-  __device__ F16Staged(const uint32_t* slot) : p(slot) {}
-  __device__ __forceinline__ float2 operator()(int comp) const { return f16_word(p[f16_site_word(comp)]); }
-};
-struct F16Global {
-  const uint32_t* p;
-  long long gs;  // words between vector groups
-  __device__ F16Global(const uint32_t* S, int t, int s3, int V3)
-      : p(S + ((long long)t * 3 * V3 + s3) * 48), gs((long long)V3 * 48) {}
-  __device__ __forceinline__ float2 operator()(int comp) const {
-    const int w = f16_site_word(comp);
-    return f16_word(__ldg(p + (w / 48) * gs + w % 48));
-  }
-};
-
-// Stage words of sites s0 .. s0+127 (all three vector groups) of timeslice t.
-__device__ __forceinline__ void stage_f16(uint32_t* dst, const __half2* S, int t, int s0, int V3) {
-  const int nsite = min(kMesonThreads, V3 - s0);
-#pragma unroll
-  for (int vg = 0; vg < 3; ++vg) {
-    const uint4* src = reinterpret_cast<const uint4*>(S + ((long long)(t * 3 + vg) * V3 + s0) * 48);
-    for (int q = threadIdx.x; q < nsite * 12; q += kMesonThreads) {
-      const uint4 v = src[q];
-      const int i = q / 12, w = (q % 12) * 4;
-      uint32_t* d = dst + i * kF16Stride + vg * 48 + w;
-      d[0] = v.x;
-      d[1] = v.y;
-      d[2] = v.z;
-      d[3] = v.w;
-    }
-  }
-}
-
-// s + e = a + b exactly (Knuth's TwoSum, six FP32 additions; the compiler
-// must not reassociate them, which CUDA does not do without fast-math).
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  const float x = __fadd_rn(a, b);
-  const float bv = __fsub_rn(x, a);
-  const float av = __fsub_rn(x, bv);
-  e = __fadd_rn(__fsub_rn(a, av), __fsub_rn(b, bv));
-  s = x;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  return v;
-}
-
-// SITES: write each channel's site value c_j(x) to sites[row(j)][t][x]
-// (complex FP32) instead of reducing it.
-template <int NQ, typename PsiT, bool SITES, bool SAME>
-__global__ void __launch_bounds__(kMesonThreads) meson_kernel(const PsiT* __restrict__ S1, const PsiT* __restrict__ S2,
-                                                              Geom g, MesonPass P, Moms M, double* __restrict__ out,
-                                                              float2* __restrict__ sites, const ScaleRecord* rec1,
-                                                              const ScaleRecord* rec2, int site_scale) {
-  extern __shared__ double2 red[];  // [warp][nch * n_mom]
-  const int s3 = blockIdx.x * kMesonThreads + threadIdx.x;
-  const int t = blockIdx.y;
-  const bool live = s3 < g.V3;
-  const int V3 = g.V3;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int nv = P.nch * M.n;
-
-  float2 Q[NQ][16];
-#pragma unroll
-  for (int q = 0; q < NQ; ++q)
-#pragma unroll
-    for (int k = 0; k < 16; ++k) Q[q][k] = make_float2(0.f, 0.f);
-
-  // the value is the stored number times 2^exp per field
-  const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
-  constexpr bool kF16 = std::is_same<PsiT, __half2>::value;
-  // float16: S2 (re-read by every mask pair) is staged in shared memory for
-  // the block's sites; S1 is read once per value, from the staged copy when
-  // S1 = S2 (SAME) and from global memory otherwise
-  uint32_t* st = reinterpret_cast<uint32_t*>(red + (SITES ? 0 : (kMesonThreads / 32) * nv));
-  if constexpr (kF16) {
-    stage_f16(st, reinterpret_cast<const __half2*>(S2), t, blockIdx.x * kMesonThreads, V3);
-    __syncthreads();
-  }
-  auto contract = [&](const auto& p1, const auto& p2) {
-#pragma unroll
-    for (int al = 0; al < 4; ++al)
-#pragma unroll
-      for (int be = 0; be < 4; ++be) {
-        float2 a[9];
-#pragma unroll
-        for (int d = 0; d < 3; ++d)
-#pragma unroll
-          for (int b = 0; b < 3; ++b) a[d * 3 + b] = p1((al * 3 + d) * 12 + be * 3 + b);
-#pragma unroll
-        for (int q = 0; q < NQ; ++q) {
-          const int al2 = al ^ P.ma[q], be2 = be ^ P.mb[q];
-          float2 acc = make_float2(0.f, 0.f);
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-#pragma unroll
-            for (int b = 0; b < 3; ++b) {
-              const float2 y = p2((al2 * 3 + d) * 12 + be2 * 3 + b);
-              const float2 x = a[d * 3 + b];
-              // acc += x * conj(y)
-              acc.x = fmaf(x.x, y.x, acc.x);
-              acc.x = fmaf(x.y, y.y, acc.x);
-              acc.y = fmaf(x.y, y.x, acc.y);
-              acc.y = fmaf(-x.x, y.y, acc.y);
-            }
-          Q[q][al * 4 + be] = acc;
-        }
-      }
-  };
-  if (live) {
-    if constexpr (kF16) {
-      const F16Staged p2(st + threadIdx.x * kF16Stride);
-      if constexpr (SAME)
-        contract(p2, p2);
-      else
-        contract(F16Global(reinterpret_cast<const uint32_t*>(S1), t, s3, V3), p2);
-    } else {
-      contract(SoASite<PsiT>(S1, t, s3, V3), SoASite<PsiT>(S2, t, s3, V3));
-    }
-  }
-
-  // exp(-i p.(x - x0)) needs the three non-decay coordinates
-  int c0 = 0, c1 = 0, c2 = 0;
-  if (!M.zero_only && live) {
-    c0 = s3 % g.sL[0];
-    c1 = (s3 / g.sL[0]) % g.sL[1];
-    c2 = s3 / (g.sL[0] * g.sL[1]);
-  }
-
-#pragma unroll
-  for (int q = 0; q < NQ; ++q) {
-    for (int j = 0; j < P.nch; ++j) {
-      if (P.q_of[j] != q) continue;
-      float2 c = make_float2(0.f, 0.f);
-#pragma unroll
-      for (int k = 0; k < 16; ++k) {
-        const float2 w = P.w[j][k];
-        c.x = fmaf(w.x, Q[q][k].x, c.x);
-        c.x = fmaf(-w.y, Q[q][k].y, c.x);
-        c.y = fmaf(w.x, Q[q][k].y, c.y);
-        c.y = fmaf(w.y, Q[q][k].x, c.y);
-      }
-      if constexpr (SITES) {
-        if (live)
-          sites[((long long)P.out_row[j] * g.Nt + t) * V3 + s3] =
-              (scale_exp && site_scale) ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
-      } else {
-        for (int m = 0; m < M.n; ++m) {
-          float2 v = c;
-          if (!M.zero_only) {
-            // phase index: sum_k n_k (x_k - o_k) V3/L_k  (mod V3), exact in integers
-            long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
-                            (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
-                            (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
-            num %= V3;
-            if (num < 0) num += V3;
-            float sn, cs;
-            sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
-            // v = c * (cs - i sn)
-            v = make_float2(c.x * cs + c.y * sn, c.y * cs - c.x * sn);
-          }
-          double re = live ? (double)v.x : 0.0;
-          double im = live ? (double)v.y : 0.0;
-          re = warp_sum(re);
-          im = warp_sum(im);
-          if (lane == 0) red[warp * nv + j * M.n + m] = make_double2(re, im);
-        }
-      }
-    }
-  }
-  if constexpr (SITES) return;
-  __syncthreads();
-  const int nwarps = kMesonThreads / 32;
-  for (int i = threadIdx.x; i < nv; i += kMesonThreads) {
-    double re = 0.0, im = 0.0;
-    for (int w = 0; w < nwarps; ++w) {
-      re += red[w * nv + i].x;
-      im += red[w * nv + i].y;
-    }
-    const int j = i / M.n, m = i % M.n;
-    const long long o = ((long long)P.out_row[j] * M.n + m) * g.Nt + t;
-    atomicAdd(out + 2 * o, ldexp(re, scale_exp));
-    atomicAdd(out + 2 * o + 1, ldexp(im, scale_exp));
-  }
-}
-
 
 // ---- staged kernel (component-major F32 / BF16 propagators) -----------------
 //
@@ -534,410 +267,10 @@ __global__ void __launch_bounds__(128) meson_fold_kernel(const double2* __restri
   }
 }
 
-
-// ---- orbit kernel: channels whose two masks are equal (ma == mb) -------------
-//
-// With ma = mb = m for every channel (the sixteen mesons Gamma_snk =
-// Gamma_src = Gamma(n) are of this kind: Gamma^dag permutes like Gamma), the
-// spin positions (alpha, beta) split into four orbits by d = alpha ^ beta,
-// and Q_m(alpha, alpha ^ d) pairs S1's block at (alpha, alpha ^ d) with S2's
-// block at (alpha ^ m, alpha ^ m ^ d), which lies in the same orbit.  A
-// thread owns (site, orbit d) for one first propagator: it keeps the orbit's
-// four 3x3 colour blocks of S_a in registers and streams the same orbit's
-// four blocks of each S_b once, each element serving all four masks.  The
-// four orbit threads of a site add their parts of each channel value through
-// shared memory.  One block stages OK_NP propagators for OK_S sites of one
-// timeslice with one tensor-map copy each (box: OK_S sites x 144
-// components, [comp][site] in shared memory).
-//
-// Pairs: first propagators ia in [0, NA) (staged index A[ia]) with second
-// propagators ib in [0, NB) (staged index B[ib]); site values of pair
-// (ia, ib) and channel j go to row rows[j] + (ia * NB + ib) * row_step.
-constexpr int kOrbMaxProps = 8;
-
-struct OrbitSet {
-  int np;                          // staged propagators
-  int na, nb;                      // first and second propagators in use (<= NA, NB)
-  int A[kOrbMaxProps], B[kOrbMaxProps];
-  int row_step;                    // SITES rows per pair (multi-propagator use)
-  int t0;                          // first timeslice of the launch (blockIdx.y = t - t0)
-  int nt_out;                      // timeslices of the site-value buffer
-  CUtensorMap map[kOrbMaxProps];   // staged propagators, box OK_S sites x 144 components
-};
-
-template <int NA, int NB, int OK_S, typename PsiT, bool SITES, bool SAME = false>
-__global__ void __launch_bounds__(OK_S * 4 * NA) meson_orbit_kernel(const __grid_constant__ OrbitSet O, Geom g,
-                                                                     MesonPass P, Moms M, float2* __restrict__ sites,
-                                                                     const ScaleRecord* rec1, const ScaleRecord* rec2,
-                                                                     int site_scale, double2* __restrict__ partial,
-                                                                     unsigned int* status, long long timeout_ns) {
-  constexpr int kThreads = OK_S * 4 * NA;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  // F32/BF16: [prop][144 comps][OK_S sites]; float16 (site-major fields):
-  // [prop][3 vector groups][OK_S sites][48 words]
-  constexpr bool kF16 = std::is_same<PsiT, __half2>::value;
-  // a float16 self pair is converted once into FP32 rows of one site's 144
-  // components (padded to 145: a warp's column reads hit distinct banks)
-  constexpr bool kF16T = kF16 && SAME && NA == 1;
-  PsiT* st = reinterpret_cast<PsiT*>(smem_raw);
-  constexpr uint32_t kPropBytes = 144u * OK_S * sizeof(PsiT);
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)O.np * kPropBytes);
-  float2* cpart = reinterpret_cast<float2*>(bar + 2);     // [4 orbits][kMaxPassCh][NA][OK_S] orbit parts
-  float2* tr = cpart + 4 * NA * kMaxPassCh * OK_S;        // [OK_S][145] (float16 self pair)
-  float2* phase = tr + (kF16T ? OK_S * 145 : 0);          // [n_mom][OK_S] (reducing form)
-  const int tid = threadIdx.x;
-  // warp-uniform orbit: thread = ((d * NA) + ia) * OK_S + site
-  const int site = tid % OK_S, ia = (tid / OK_S) % NA, d = tid / (OK_S * NA);
-  const int s0 = blockIdx.x * OK_S, t = blockIdx.y;  // t: timeslice O.t0 + t of the lattice
-  const bool act = ia < O.na;                         // threads of an unused first propagator idle
-  const int s3 = s0 + site;
-  const bool live = s3 < g.V3;
-  const int V3 = g.V3;
-  const uint32_t bar_a = ptx::smem_addr(bar);
-
-  if (tid == 0) {
-    ptx::mbar_init(bar_a, 1);
-    ptx::fence_mbar_init();
-    ptx::mbar_arrive_expect_tx(bar_a, (uint32_t)O.np * kPropBytes);
-    for (int i = 0; i < O.np; ++i) {
-      if constexpr (kF16)
-        ptx::tensor_g2s_3d(ptx::smem_addr(smem_raw + (size_t)i * kPropBytes), &O.map[i], 0, s0, (O.t0 + t) * 3,
-                           bar_a);
-      else
-        ptx::tensor_g2s_2d(ptx::smem_addr(smem_raw + (size_t)i * kPropBytes), &O.map[i], s0, (O.t0 + t) * 144, bar_a);
-    }
-  }
-  __syncthreads();
-  const bool ok = ptx::mbar_wait_bounded(bar_a, 0, timeout_ns);
-  if (!__syncthreads_and(ok ? 1 : 0)) {
-    if (tid == 0) {
-      atomicOr(status, kStatusFullWait);
-      if (!ptx::mbar_wait_bounded(bar_a, 0, timeout_ns)) atomicOr(status, kStatusDrain);
-    }
-    return;
-  }
-  if constexpr (kF16T) {
-    // [3 vector groups][OK_S sites][48 words] -> [site][component], FP32;
-    // word w of group vg is vector v = 16 vg + w / 3, sink colour w % 3
-    const uint32_t* L = reinterpret_cast<const uint32_t*>(smem_raw);
-    for (int idx = tid; idx < 3 * OK_S * 48; idx += kThreads) {
-      const int vg = idx / (OK_S * 48), r = idx - vg * (OK_S * 48), ss = r / 48, w = r - ss * 48;
-      const int v = vg * 16 + w / 3, c = w % 3;
-      tr[ss * 145 + ((v / 12) * 3 + c) * 12 + v % 12] = f16_word(L[idx]);
-    }
-    __syncthreads();
-  }
-  // element (comp) of staged propagator i at this thread's site
-  auto elem = [&](int i, int comp) -> u64 {
-    if constexpr (kF16T) {
-      (void)i;
-      return lds_pair_st(tr + site * 145 + comp);
-    } else if constexpr (kF16) {
-      const int w = f16_site_word(comp);  // vector group * 48 + word
-      return lds_pair_st(st + (size_t)i * 144 * OK_S + ((w / 48) * OK_S + site) * 48 + w % 48);
-    } else {
-      return lds_pair_st(st + ((size_t)i * 144 + comp) * OK_S + site);
-    }
-  };
-  // component of (spin row al, spin column be, colour row c, colour column e)
-  auto comp_of = [](int al, int be, int c, int e) { return (al * 3 + c) * 12 + be * 3 + e; };
-
-  if constexpr (!SITES) {
-    // phases of the block's sites for the momentum sums, read after the
-    // barrier that follows the orbit parts
-    if (d == 1 && !M.zero_only) {
-      int c0 = 0, c1 = 0, c2 = 0;
-      if (live) {
-        c0 = s3 % g.sL[0];
-        c1 = (s3 / g.sL[0]) % g.sL[1];
-        c2 = s3 / (g.sL[0] * g.sL[1]);
-      }
-      for (int m = 0; m < M.n; ++m) {
-        long long num = (long long)M.k[m][0] * (((c0 - M.origin[0]) % g.sL[0] + g.sL[0]) % g.sL[0]) * (V3 / g.sL[0]) +
-                        (long long)M.k[m][1] * (((c1 - M.origin[1]) % g.sL[1] + g.sL[1]) % g.sL[1]) * (V3 / g.sL[1]) +
-                        (long long)M.k[m][2] * (((c2 - M.origin[2]) % g.sL[2] + g.sL[2]) % g.sL[2]) * (V3 / g.sL[2]);
-        num %= V3;
-        if (num < 0) num += V3;
-        float sn, cs;
-        sincospif(2.0f * (float)num / (float)V3, &sn, &cs);
-        phase[m * OK_S + site] = make_float2(cs, sn);
-      }
-    }
-  }
-  // this thread's orbit blocks of S_a: x[al][c*3+e] at (al, al ^ d)
-  u64 x[4][9];
-  const int pa = O.A[act ? ia : 0];
-#pragma unroll
-  for (int al = 0; al < 4; ++al)
-#pragma unroll
-    for (int k = 0; k < 9; ++k) x[al][k] = elem(pa, comp_of(al, al ^ d, k / 3, k % 3));
-
-  for (int ib = 0; ib < O.nb; ++ib) {
-    const int pb = O.B[ib];
-    // Q as (re, im) and i Q = (-im, re)
-    u64 Qz[4][4], Qi[4][4];
-    if constexpr (SAME) {
-      // S2 = S1: S2's orbit blocks are this thread's x, and
-      // Q_m(al ^ m, .) = conj(Q_m(al, .)): |x|^2 sums for m = 0 and one
-      // product per pair {al, al ^ m} (al the smaller) for m = 1, 2, 3
-      (void)pb;
-      u64 P0[4], Pp[3][2], Rp[3][2];
-#pragma unroll
-      for (int al = 0; al < 4; ++al) P0[al] = 0ull;
-#pragma unroll
-      for (int m = 1; m < 4; ++m) Pp[m - 1][0] = Pp[m - 1][1] = Rp[m - 1][0] = Rp[m - 1][1] = 0ull;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        u64 xs[4];
-#pragma unroll
-        for (int b = 1; b < 4; ++b) {
-          const float2 v = unpack2(x[b][k]);
-          xs[b] = pack2(v.y, v.x);
-        }
-#pragma unroll
-        for (int al = 0; al < 4; ++al) P0[al] = fma2(x[al][k], x[al][k], P0[al]);
-#pragma unroll
-        for (int m = 1; m < 4; ++m)
-#pragma unroll
-          for (int q = 0; q < 2; ++q) {
-            // the pair's smaller member: m = 1: 0, 2; m = 2: 0, 1; m = 3: 0, 1
-            const int lo = m == 1 ? 2 * q : q, hi = lo ^ m;
-            Pp[m - 1][q] = fma2(x[lo][k], x[hi][k], Pp[m - 1][q]);
-            Rp[m - 1][q] = fma2(x[lo][k], xs[hi], Rp[m - 1][q]);
-          }
-      }
-#pragma unroll
-      for (int al = 0; al < 4; ++al) {
-        const float2 a = unpack2(P0[al]);
-        const float re = a.x + a.y;
-        Qz[al][0] = pack2(re, 0.f);
-        Qi[al][0] = pack2(0.f, re);
-      }
-#pragma unroll
-      for (int m = 1; m < 4; ++m)
-#pragma unroll
-        for (int q = 0; q < 2; ++q) {
-          const int lo = m == 1 ? 2 * q : q, hi = lo ^ m;
-          const float2 a = unpack2(Pp[m - 1][q]), b = unpack2(Rp[m - 1][q]);
-          const float re = a.x + a.y, im = b.y - b.x;
-          Qz[lo][m] = pack2(re, im);
-          Qi[lo][m] = pack2(-im, re);
-          Qz[hi][m] = pack2(re, -im);
-          Qi[hi][m] = pack2(im, re);
-        }
-    } else {
-    // Pm[al][m] and Rm[al][m]: packed parts of Q_m(al, al ^ d) = sum x conj(y)
-    // for mask m = 0..3 (all four; every index compile-time), re = P.x + P.y,
-    // im = R.y - R.x
-    u64 Pm[4][4], Rm[4][4];
-#pragma unroll
-    for (int al = 0; al < 4; ++al)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) Pm[al][m] = Rm[al][m] = 0ull;
-#pragma unroll
-    for (int be = 0; be < 4; ++be) {  // S_b's orbit block at (be, be ^ d)
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const u64 y = live ? elem(pb, comp_of(be, be ^ d, k / 3, k % 3)) : 0ull;
-        const float2 yv = unpack2(y);
-        const u64 ys = pack2(yv.y, yv.x);
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {  // S1 block (al, al ^ d) pairs with S2 block (al ^ m, al ^ m ^ d)
-          const int al = be ^ m;
-          Pm[al][m] = fma2(x[al][k], y, Pm[al][m]);
-          Rm[al][m] = fma2(x[al][k], ys, Rm[al][m]);
-        }
-      }
-    }
-#pragma unroll
-    for (int al = 0; al < 4; ++al)
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        const float2 a = unpack2(Pm[al][m]), b = unpack2(Rm[al][m]);
-        const float re = a.x + a.y, im = b.y - b.x;
-        Qz[al][m] = pack2(re, im);
-        Qi[al][m] = pack2(-im, re);
-      }
-    }
-    // this orbit's part of every channel: sum_al w_j(al, al ^ d) Q_m(al, al ^ d)
-    // for the channels j of mask m (host-grouped: P.mlo[m] <= j < P.mhi[m])
-    if (act) {
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        for (int j = P.mlo[m]; j < P.mhi[m]; ++j) {
-          u64 c = 0ull;
-#pragma unroll
-          for (int al = 0; al < 4; ++al) {
-            const int k = al * 4 + (al ^ d);
-            c = fma2(P.wre[j][k], Qz[al][m], c);
-            c = fma2(P.wim[j][k], Qi[al][m], c);
-          }
-          cpart[((d * kMaxPassCh + j) * NA + ia) * OK_S + site] = unpack2(c);  // a warp's lanes: contiguous
-        }
-    }
-    __syncthreads();
-    if constexpr (SITES) {
-      // the four orbits' parts of each (first propagator, channel, site), shared by all threads
-      const int scale_exp = rec1 ? rec1->exp + rec2->exp : 0;
-      for (int u = tid; u < P.nch * NA * OK_S; u += kThreads) {
-        const int us = u % OK_S, ua = (u / OK_S) % NA, uj = u / (OK_S * NA);
-        if (ua >= O.na) continue;
-        float2 c = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const float2 v = cpart[((o * kMaxPassCh + uj) * NA + ua) * OK_S + us];
-          c.x += v.x;
-          c.y += v.y;
-        }
-        const int us3 = s0 + us;
-        if (us3 < V3) {
-          const long long row = (long long)P.out_row[uj] + (long long)(ua * O.nb + ib) * O.row_step;
-          sites[(row * O.nt_out + t) * V3 + us3] =
-              (scale_exp && site_scale) ? make_float2(ldexpf(c.x, scale_exp), ldexpf(c.y, scale_exp)) : c;
-        }
-      }
-    } else {
-      // timeslice/momentum sums of the block's sites (NA = NB = 1): thread
-      // (channel tid / TPC, sites 4 (tid % TPC) .. +3) adds the four
-      // orbits' parts of its sites, multiplies them by the phases and sums
-      // them in two-float arithmetic; the channel's TPC = OK_S / 4 lanes
-      // finish each sum with a butterfly
-      constexpr int TPC = OK_S / 4;
-      static_assert(SITES || (NA == 1 && OK_S % 4 == 0 && TPC <= 32 && (TPC & (TPC - 1)) == 0),
-                    "the reducing form takes one pair and 4 sites per lane, a power-of-two lanes per channel");
-      const int uj = tid / TPC, g4 = (tid % TPC) * 4;
-      const int nv = P.nch * M.n;
-      float2 cs[4];
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        float2 c = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int o = 0; o < 4; ++o) {
-          const float2 v = cpart[(o * kMaxPassCh + uj) * OK_S + g4 + q];
-          c.x += v.x;
-          c.y += v.y;
-        }
-        cs[q] = (uj < P.nch && s0 + g4 + q < V3) ? c : make_float2(0.f, 0.f);
-      }
-      for (int m = 0; m < M.n; ++m) {
-        float2 hi = make_float2(0.f, 0.f), lo = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-          float2 a = cs[q];
-          if (!M.zero_only) {
-            const float2 pa2 = phase[m * OK_S + g4 + q];
-            a = make_float2(a.x * pa2.x + a.y * pa2.y, a.y * pa2.x - a.x * pa2.y);  // c (cs - i sn)
-          }
-          float ex, ey;
-          two_sum(hi.x, a.x, hi.x, ex);
-          two_sum(hi.y, a.y, hi.y, ey);
-          lo.x += ex;
-          lo.y += ey;
-        }
-#pragma unroll
-        for (int o = TPC / 2; o > 0; o >>= 1) {
-          const float hx = __shfl_xor_sync(0xffffffffu, hi.x, o), lx = __shfl_xor_sync(0xffffffffu, lo.x, o);
-          const float hy = __shfl_xor_sync(0xffffffffu, hi.y, o), ly = __shfl_xor_sync(0xffffffffu, lo.y, o);
-          float ex, ey;
-          two_sum(hi.x, hx, hi.x, ex);
-          two_sum(hi.y, hy, hi.y, ey);
-          lo.x = lo.x + lx + ex;
-          lo.y = lo.y + ly + ey;
-        }
-        if (tid % TPC == 0 && uj < P.nch)
-          partial[((long long)t * gridDim.x + blockIdx.x) * nv + uj * M.n + m] =
-              make_double2((double)hi.x + (double)lo.x, (double)hi.y + (double)lo.y);
-      }
-    }
-    __syncthreads();  // cpart is reused by the next second propagator
-  }
-}
-
-
-// The orbit kernel for one pass of one pair (S1, S2), or QDPG_ERR_UNSUPPORTED
-// where it does not apply (a channel with different masks, two different
-// float16 propagators, a component row not a multiple of 16 bytes, no
-// tensor-map support).
-// Sites per block, for site-value output and for the reducing form (32 each:
-// measured faster than 16-site blocks at 16^3x32 and 24^3x48).
-constexpr int kOrbitSitesS = 32;
-constexpr int kOrbitSitesR = 32;
-
-int launch_orbit_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
-                      float2* sites, cudaStream_t s, int site_scale) {
-  const int kS = sites ? kOrbitSitesS : kOrbitSitesR;
-  const Geom& g = S1->g;
-  const bool bf = S1->prec == QDPG_BF16;
-  const bool h16 = S1->prec == QDPG_F16;
-  const bool same = S1->data == S2->data;
-  if (S1->prec != QDPG_F32 && !bf && !(h16 && same)) return QDPG_ERR_UNSUPPORTED;  // float16: self pairs
-  for (int q = 0; q < P.nq; ++q)
-    if (P.ma[q] != P.mb[q]) return QDPG_ERR_UNSUPPORTED;
-  const int esize = (bf || h16) ? 4 : 8;
-  if (!h16 && ((long long)g.V3 * esize) % 16 != 0) return QDPG_ERR_UNSUPPORTED;
-  OrbitSet O{};
-  O.np = same ? 1 : 2;
-  O.na = O.nb = 1;
-  O.A[0] = 0;
-  O.B[0] = same ? 0 : 1;
-  O.row_step = 0;
-  O.t0 = 0;
-  O.nt_out = g.Nt;
-  const qdpg_field* staged[2] = {S1, S2};
-  // F32/BF16: (site; component row) boxes of kS x 144; float16: (word; site;
-  // timeslice-vector-group) boxes of 48 x kS x 3
-  for (int i = 0; i < O.np; ++i)
-    if (reinterpret_cast<uintptr_t>(staged[i]->data) % 16 != 0 ||
-        !(h16 ? encode_map_3d(&O.map[i], staged[i]->data, 4, 48, (uint64_t)g.V3, (uint64_t)g.Nt * 3, 48 * 4,
-                              (uint64_t)g.V3 * 48 * 4, 48, kS, 3)
-              : encode_map_2d(&O.map[i], staged[i]->data, esize, (uint64_t)g.V3, (uint64_t)g.Nt * 144,
-                              (uint64_t)g.V3 * esize, kS, 144)))
-      return QDPG_ERR_UNSUPPORTED;
-  unsigned int* status = device_status_word();
-  if (!status) return QDPG_ERR_UNSUPPORTED;
-  const size_t smem = (size_t)O.np * 144 * kS * esize + 16 + (size_t)4 * kMaxPassCh * kS * sizeof(float2) +
-                      (h16 ? (size_t)kS * 145 * sizeof(float2) : 0) + (size_t)M.n * kS * sizeof(float2);
-  dim3 grid((g.V3 + kS - 1) / kS, g.Nt);
-  void* partial = nullptr;
-  if (!sites) {
-    const int arc = dev_alloc(&partial, sizeof(double2) * (size_t)grid.x * g.Nt * P.nch * M.n, s,
-                              "meson_2pt partial sums");
-    if (arc != QDPG_OK) return arc;
-  }
-  ProfScope prof("meson_2pt", s);
-  cudaError_t e = cudaSuccess;
-#define QDPG_ORBIT(T, SITES)                                                                                   \
-  do {                                                                                                         \
-    constexpr int KS = SITES ? kOrbitSitesS : kOrbitSitesR;                                                    \
-    auto k = same ? meson_orbit_kernel<1, 1, KS, T, SITES, true> : meson_orbit_kernel<1, 1, KS, T, SITES>;     \
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
-    if (e == cudaSuccess)                                                                                      \
-      k<<<grid, kS * 4, smem, s>>>(O, g, P, M, sites, S1->rec, S2->rec, site_scale,                            \
-                                   static_cast<double2*>(partial), status, wait_timeout_ns());                  \
-  } while (0)
-  if (h16) {
-    if (sites) QDPG_ORBIT(__half2, true);
-    else QDPG_ORBIT(__half2, false);
-  } else if (bf) {
-    if (sites) QDPG_ORBIT(__nv_bfloat162, true);
-    else QDPG_ORBIT(__nv_bfloat162, false);
-  } else {
-    if (sites) QDPG_ORBIT(float2, true);
-    else QDPG_ORBIT(float2, false);
-  }
-#undef QDPG_ORBIT
-  if (e != cudaSuccess) {
-    dev_free(partial, s);
-    return fail(QDPG_ERR_CUDA, "meson_2pt: smem attribute: %s", cudaGetErrorString(e));
-  }
-  int rc = check_launch("meson_2pt");
-  if (rc == QDPG_OK && !sites) {
-    meson_fold_kernel<<<dim3(P.nch * M.n, g.Nt), 128, 0, s>>>(static_cast<const double2*>(partial), (int)grid.x, P,
-                                                              M.n, g.Nt, out, S1->rec, S2->rec);
-    rc = check_launch("meson_2pt fold");
-  }
-  dev_free(partial, s);
-  return rc;
+int launch_meson_fold(const double2* partial, int nbx, const MesonPass& P, int nmom, int Nt, double* out,
+                      const ScaleRecord* r1, const ScaleRecord* r2, cudaStream_t s) {
+  meson_fold_kernel<<<dim3(P.nch * nmom, Nt), 128, 0, s>>>(partial, nbx, P, nmom, Nt, out, r1, r2);
+  return check_launch("meson_2pt fold");
 }
 
 // The staged kernel for one pass, or QDPG_ERR_UNSUPPORTED where it does not
@@ -1029,7 +362,6 @@ inline unsigned long long pack_host(float lo, float hi) {
 
 int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const qdpg_field* S2, double* out,
                 float2* sites, cudaStream_t s, int site_scale = 1) {
-  const Geom& g = S1->g;
   const int form = debug_meson_form();  // 0: best available, 1: staged, 2: global reads
   if (form == 0) {
     const int rc = launch_orbit_pass(P, M, S1, S2, out, sites, s, site_scale);
@@ -1039,47 +371,10 @@ int launch_pass(const MesonPass& P, const Moms& M, const qdpg_field* S1, const q
     const int rc = launch_staged_pass(P, M, S1, S2, out, sites, s, site_scale);
     if (rc != QDPG_ERR_UNSUPPORTED) return rc;
   }
-  dim3 grid((g.V3 + kMesonThreads - 1) / kMesonThreads, g.Nt);
-  size_t smem = sites ? 0 : (size_t)(kMesonThreads / 32) * P.nch * M.n * sizeof(double2);
-  const bool bf = S1->prec == QDPG_BF16;
-  const bool h16 = S1->prec == QDPG_F16;
-  const bool same = S1->data == S2->data;
-  if (h16) smem += (size_t)kMesonThreads * kF16Stride * sizeof(uint32_t);  // staged S2
-  ProfScope prof("meson_2pt", s);
-#define QDPG_MESON_KERNEL(NQ, T, SITES, SAME)                                                          \
-  do {                                                                                                 \
-    auto k = meson_kernel<NQ, T, SITES, SAME>;                                                         \
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); \
-    k<<<grid, kMesonThreads, smem, s>>>(static_cast<const T*>(S1->data), static_cast<const T*>(S2->data), g, P, M, \
-                                        out, sites, S1->rec, S2->rec, site_scale);                     \
-  } while (0)
-#define QDPG_MESON_LAUNCH(NQ)                                                  \
-  do {                                                                         \
-    if (bf) {                                                                  \
-      if (sites) QDPG_MESON_KERNEL(NQ, __nv_bfloat162, true, false);           \
-      else QDPG_MESON_KERNEL(NQ, __nv_bfloat162, false, false);                \
-    } else if (h16) {                                                          \
-      if (sites && same) QDPG_MESON_KERNEL(NQ, __half2, true, true);           \
-      else if (sites) QDPG_MESON_KERNEL(NQ, __half2, true, false);             \
-      else if (same) QDPG_MESON_KERNEL(NQ, __half2, false, true);              \
-      else QDPG_MESON_KERNEL(NQ, __half2, false, false);                       \
-    } else {                                                                   \
-      if (sites) QDPG_MESON_KERNEL(NQ, float2, true, false);                   \
-      else QDPG_MESON_KERNEL(NQ, float2, false, false);                        \
-    }                                                                          \
-  } while (0)
-  switch (P.nq) {
-    case 1: QDPG_MESON_LAUNCH(1); break;
-    case 2: QDPG_MESON_LAUNCH(2); break;
-    case 3: QDPG_MESON_LAUNCH(3); break;
-    default: QDPG_MESON_LAUNCH(4); break;
-  }
-#undef QDPG_MESON_LAUNCH
-#undef QDPG_MESON_KERNEL
-  return check_launch("meson_2pt");
+  return launch_global_pass(P, M, S1, S2, out, sites, s, site_scale);
 }
 
-}  // namespace
+}  // namespace meson
 
 }  // namespace qdpg
 
@@ -1088,6 +383,8 @@ using namespace qdpg;
 namespace qdpg {
 namespace {
 
+using namespace meson;
+using namespace gamma_host;
 
 // Channel masks and weights (the XOR-mask form of the trace, see the top of
 // this file), sorted by mask pair.
@@ -1259,6 +556,8 @@ int qdpg_meson_sites(qdpg_field_t S1, qdpg_field_t S2, const int* gamma_snk, con
 namespace qdpg {
 namespace {
 
+using namespace meson;
+
 struct RecTable {
   const ScaleRecord* r[kOrbMaxProps];
 };
@@ -1276,7 +575,7 @@ __global__ void pair_exp_kernel_t(RecTable R, int n, int n_chan, int* __restrict
 extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, const int* gamma_snk,
                                     const int* gamma_src, int n_chan, const int* moms, int n_mom, const int origin[4],
                                     double* out_dev, void* stream) {
-  constexpr int kS = 4;  // sites per block: 4 sites x 4 orbits x 8 first propagators = 128 threads
+  constexpr int kS = kMultiSites;  // sites per block: 4 sites x 4 orbits x 8 first propagators = 128 threads
   if (!props || !gamma_snk || !gamma_src || !moms || !out_dev) return fail(QDPG_ERR_ARG, "meson_2pt_multi: null argument");
   if (n_props < 1 || n_props > kOrbMaxProps)
     return fail(QDPG_ERR_ARG, "meson_2pt_multi: n_props %d outside 1..%d", n_props, kOrbMaxProps);
@@ -1360,23 +659,9 @@ extern "C" int qdpg_meson_2pt_multi(const qdpg_field_t* props, int n_props, cons
     O.t0 = t0;
     O.nt_out = nt;
     dim3 grid((g.V3 + kS - 1) / kS, nt);
-    cudaError_t e = cudaSuccess;
     {
       ProfScope prof("meson_2pt", s);
-#define QDPG_MULTI(T_)                                                                                          \
-  do {                                                                                                         \
-    auto k = meson_orbit_kernel<kOrbMaxProps, kOrbMaxProps, kS, T_, true>;                                     \
-    e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);                      \
-    if (e == cudaSuccess)                                                                                      \
-      k<<<grid, kS * 4 * kOrbMaxProps, smem, s>>>(O, g, P, M, static_cast<float2*>(sites), nullptr, nullptr, 0, \
-                                                  nullptr, status, wait_timeout_ns());                          \
-  } while (0)
-      if (h16) QDPG_MULTI(__half2);
-      else if (bf) QDPG_MULTI(__nv_bfloat162);
-      else QDPG_MULTI(float2);
-#undef QDPG_MULTI
-      if (e != cudaSuccess) rc = fail(QDPG_ERR_CUDA, "meson_2pt_multi: smem attribute: %s", cudaGetErrorString(e));
-      else rc = check_launch("meson_2pt_multi");
+      rc = launch_orbit_multi(O, g, P, M, static_cast<float2*>(sites), props[0]->prec, smem, grid, s, status);
     }
     if (rc != QDPG_OK) break;
     Geom gb = g;  // the batch as a lattice of nt timeslices for the projection's row layout
